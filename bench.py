@@ -1,0 +1,313 @@
+"""Benchmark of the fused stream-and-collide sweep (GLUPS, HBM GB/s).
+
+Workload: 3D periodic 256^3 grid, D3Q111 velocity set with the N=5
+equilibrium, binary64 populations, source = 64 periodic Gaussians (sigma 2
+cells, centres from SplitMix64 seed 0, charges alternating +-1, mean
+removed), tau_lb from Kn = 0.2.  One benchmark step = 32 sweeps followed by
+the binary64 relative-L2 residual check (one pass of the whole hot path: pull,
+density, BGK relaxation, source, store, residual).  The populations (2 x 14.9
+GB) are far larger than L2, so no flush is needed between steps.
+
+``e2e``: the same metric for a complete solve to rel. residual 1e-10 through
+``pkr_solve`` with host buffers (H2D of rho and D2H of Phi inside the timed
+region).  ``cpu_baseline``: the oracle (serial C) on a 16-plane slab of the same
+source.  ``--impl reference`` times that oracle alone, as the reference arm.
+
+Multi-GPU: the path does not shard (one grid per GPU, no collectives), so N
+ranks run N independent replicas; value = all ranks' site updates / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (256, 256, 256)
+LATTICE, ORDER, KN = "D3Q111", 5, 0.2
+PRECISION = "fp64"
+SWEEPS_PER_STEP = 32
+SLAB = 16            # planes of the CPU-baseline sample
+REF_SLAB = 2         # planes per reference-arm step
+METRIC = "GLUPS (site updates/s, 1e9) of the fused sweep"
+WORKLOAD = "poisson3d_256cube_d3q111_n5_fp64_64gauss_sigma2_seed0_kn0.2"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def source():
+    from paper_1504_05869_gb300.workloads import stiff_source
+    rho, _ = stiff_source(SHAPE, count=64, sigma=2.0, seed=0)
+    return rho
+
+
+def configure(args):
+    """Smaller or different cases (profiling, sweeps of sizes); the default is
+    the headline workload."""
+    global SHAPE, LATTICE, ORDER, PRECISION, WORKLOAD
+    if args.size:
+        SHAPE = (args.size,) * 3
+    LATTICE, ORDER, PRECISION = args.lattice, args.order, args.precision
+    if (SHAPE, LATTICE, ORDER, PRECISION) != ((256, 256, 256), "D3Q111", 5, "fp64"):
+        n = SHAPE[0]
+        WORKLOAD = (f"poisson3d_{n}cube_{LATTICE.lower()}_n{ORDER}_{PRECISION}"
+                    f"_64gauss_sigma2_seed0_kn0.2")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(rho, tau):
+    """The oracle (serial C, one core) on a 16-plane slab of the source."""
+    import oracle
+    slab = np.ascontiguousarray(rho[:SLAB])
+    t0 = time.perf_counter()
+    oracle.solve(slab, LATTICE, ORDER, tau_lb=tau, max_steps=1)
+    dt = time.perf_counter() - t0
+    return {"value": slab.size / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"1 step (source prep + collide/stream + density) on a "
+                      f"{SLAB}x256x256 slab of the same source, serial C, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle timed on the host, each step one oracle step
+    on a 2-plane slab of the benchmark's source."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    rho = source()
+    lat = oracle.lattice(LATTICE, ORDER)
+    tau = oracle.tau_from_knudsen(KN, SHAPE[::-1], lat.cs2)
+    slab = np.ascontiguousarray(rho[:REF_SLAB])
+    for _ in range(args.warmup):
+        oracle.solve(slab, LATTICE, ORDER, tau_lb=tau, max_steps=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve(slab, LATTICE, ORDER, tau_lb=tau, max_steps=1)
+    dt = time.perf_counter() - t0
+    val = slab.size * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{REF_SLAB}x256x256 slab, 1 step"},
+            "cpu_baseline": {"value": val, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"one oracle step on a {REF_SLAB}x256x256 slab per "
+                                       "benchmark step"},
+            "e2e": {"value": val, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+
+    rho = source()
+    V = rho.size
+    stream = torch.cuda.Stream()
+    prob = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN, tol=0.0,
+                      check_every=SWEEPS_PER_STEP, max_sweeps=10 ** 9, precision=PRECISION)
+    r_dev = torch.from_numpy(rho).cuda()
+    with torch.cuda.stream(stream):
+        plan = pk.Plan(prob, stream=stream)
+        plan.load_source(r_dev)
+    Q = {"D3Q111": 111, "D3Q19": 19}[LATTICE]
+    esize = 8 if PRECISION == "fp64" else 4
+    tau = None
+
+    def step():
+        rc, st = plan.run(SWEEPS_PER_STEP)
+        return st
+
+    for _ in range(args.warmup):
+        st = step()
+    tau = st["tau_lb"]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    dev_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([dev_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+        dist.barrier()
+    sweeps = args.steps * SWEEPS_PER_STEP
+    glups = world * V * sweeps / (dev_ms * 1e-3) / 1e9
+    bytes_site = 2 * Q * esize + esize
+    # per-launch: plain sweeps move 2*Q*8 + 8 bytes per site
+    launch_ms = dev_ms / sweeps
+    achieved = V * bytes_site / (launch_ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    plan.close()
+
+    # end to end: full solve to 1e-10 through pkr_solve with host buffers
+    e2e = None
+    if not args.no_e2e:
+        rho_h = torch.from_numpy(rho).pin_memory()
+        phi_h = torch.empty_like(rho_h).pin_memory()
+        eprob = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN, tol=1e-10, tol_kind="rel_l2",
+                           check_every=SWEEPS_PER_STEP, max_sweeps=200000,
+                           precision=PRECISION)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            rc, est = pk.solve(rho_h.numpy(), phi_h.numpy(), eprob, stream=stream)
+        torch.cuda.synchronize()
+        e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_s = float(t.item())
+        e2e = {"value": world * V * est["launches"] / e_s / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": V * 8, "d2h_bytes_per_step": V * 8,
+               "solve": {"sweeps": est["sweeps"], "residual": est["residual"],
+                         "status": rc, "seconds": e_s, "tol": 1e-10}}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(rho, tau)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if PRECISION == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(SHAPE), "lattice": LATTICE,
+                       "order": ORDER, "knudsen": KN, "tau_lb": tau,
+                       "sweeps_per_step": SWEEPS_PER_STEP, "residual_check": "rel_l2 fp64",
+                       "l2": "inputs larger than L2 (2 x 14.9 GB populations)",
+                       "parallelism": f"replicas x{world}"},
+            "hbm_gbs": V * bytes_site * sweeps * world / (dev_ms * 1e-3) / 1e9,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": None, "peak_source": peak_src,
+                         "kernel": f"sweep_kernel<{LATTICE},"
+                                   f"{'double' if PRECISION == 'fp64' else 'float'}>",
+                         "algorithmic_bytes_per_launch": V * bytes_site},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": args.steps * (SWEEPS_PER_STEP + 1),
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pkr", choices=["pkr", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--size", type=int, default=0, help="cube edge (default 256)")
+    ap.add_argument("--lattice", default="D3Q111", choices=["D3Q111", "D3Q19"])
+    ap.add_argument("--order", type=int, default=5)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    args = ap.parse_args()
+    configure(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * pkr.h -- C ABI of the GB300 high-order kinetic relaxation Poisson solver.
+ *
+ * The library solves the periodic Poisson problem
+ *     lap Phi = -(rho - <rho>) / eps
+ * (the paper's Eq. poisson1, Sec. "Numerical Results") as the steady state of
+ * a lattice-Boltzmann diffusion scheme whose equilibrium and source weights
+ * are Hermite expansions truncated at order N so that the unwanted high-order
+ * moments vanish (Sec. "Kinetic approach to the Poisson equation", Eqs. CON,
+ * equilibrium2, omega:eq, chi:eq, omega:eq3, chi:eq3).  One time step at every
+ * site x, for all discrete velocities v_i:
+ *     g_i(x)     = f_i(x - v_i)                       streaming (periodic)
+ *     Phi(x)     = sum_i g_i(x)                       zeroth moment
+ *     f'_i(x)    = g_i(x) - (g_i(x) - phi_i Phi(x))/tau_lb + chi_i S(x)
+ * with S = (rho - <rho>) c_s^2 (tau_lb - 1/2) / eps (text after Eq. poisson1)
+ * and populations starting at zero.  Steps repeat until the change of Phi
+ * over one step drops below a tolerance.  Everything runs in this library's
+ * CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - Return value: a pkr_status (0 = PKR_OK, negative = error).  No call
+ *     throws or aborts; on an error no output buffer is written unless the
+ *     entry point says otherwise.
+ *   - Grids are given as n[3] = {nx, ny, nz}; unused dimensions are 1.  Site
+ *     arrays (rho, Phi) are dense, x fastest: index (z*ny + y)*nx + x.
+ *   - "Device pointer" means memory of the GPU that is current when the call
+ *     is made; "host pointer" means ordinary (pageable or pinned) host memory.
+ *   - The caller owns every buffer it passes in; the library owns what a plan
+ *     allocates and frees it in pkr_plan_destroy.
+ *   - stream: a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Calls that return results synchronise that stream.
+ */
+#ifndef PKR_H
+#define PKR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pkr_status {
+    PKR_OK = 0,
+    PKR_EINVAL = -1,     /* bad argument: sizes, lattice/order, tau, NaN in rho */
+    PKR_ENOMEM = -2,     /* device allocation failed or over the budget */
+    PKR_EUNSTABLE = -3,  /* tau_lb below the lattice's stability bound */
+    PKR_ENOCONV = -4,    /* max_sweeps reached before tol (Phi still written) */
+    PKR_EDIVERGED = -5,  /* residual became non-finite or grew without bound */
+    PKR_ECUDA = -6,      /* a CUDA runtime call failed */
+    PKR_EBUSY = -7       /* a ticket has not finished yet */
+} pkr_status;
+
+/* Velocity sets.  1D sets: the paper's Appendix (N=3 set {0,+-1,+-3}, N=5 set
+ * {0,+-1,+-2,+-3,+-5}, N=7 set {0,..,+-6}); 2D sets: their tensor products;
+ * D3Q19: standard first-order LB; D3Q111: Appendix Table "vector2". */
+typedef enum pkr_lattice {
+    PKR_D1Q5 = 0, PKR_D1Q9 = 1, PKR_D1Q13 = 2,
+    PKR_D2Q25 = 3, PKR_D2Q81 = 4, PKR_D2Q169 = 5,
+    PKR_D3Q19 = 6, PKR_D3Q111 = 7
+} pkr_lattice;
+
+/* Storage of the populations.  FP64: stored and updated in binary64.
+ * FP32: stored and updated in binary32 (Phi, residual norms and the source
+ * mean stay binary64). */
+typedef enum pkr_precision { PKR_FP64 = 0, PKR_FP32 = 1 } pkr_precision;
+
+/* Stopping rule: change of Phi over one step, checked every check_every
+ * steps.  MAX_ABS: max_x |Phi^t - Phi^(t-1)|.  REL_L2: ||dPhi||_2/||Phi^t||_2. */
+typedef enum pkr_tol_kind { PKR_TOL_MAX_ABS_DPHI = 0, PKR_TOL_REL_L2_DPHI = 1 } pkr_tol_kind;
+
+typedef struct pkr_problem {
+    int32_t dim;          /* 1, 2 or 3; must match the lattice */
+    int32_t lattice;      /* pkr_lattice */
+    int64_t n[3];         /* periodic grid {nx, ny, nz}, each >= 1, n[k]=1 for k>=dim */
+    int32_t order;        /* expansion order N in {1,3,5,7}; <= the lattice's maximum */
+    int32_t precision;    /* pkr_precision */
+    double tau_lb;        /* relaxation time; > 0.5 used as is, <= 0 => from knudsen */
+    double knudsen;       /* Kn = c_s (tau_lb - 1/2) / min(n): used if tau_lb <= 0 */
+    double epsilon;       /* permittivity eps > 0 (0 means 1) */
+    double tol;           /* stop when the residual < tol; <= 0: run max_sweeps steps */
+    int32_t tol_kind;     /* pkr_tol_kind */
+    int32_t check_every;  /* steps between residual checks (<= 0: 32) */
+    int64_t max_sweeps;   /* upper bound on the steps taken (>= 1) */
+} pkr_problem;
+
+typedef struct pkr_stats {
+    int64_t sweeps;          /* steps t such that the returned Phi is Phi^t */
+    int64_t launches;        /* sweep kernels launched */
+    double residual;         /* last checked change of Phi (-1 if none) */
+    double rho_mean_removed; /* <rho> subtracted before solving */
+    double tau_lb;           /* relaxation time used */
+    double cs2;              /* lattice c_s^2 */
+    double wall_ms;          /* host wall time of the call */
+    double glups;            /* site updates / wall time, 1e9 / s */
+    double hbm_gbs;          /* algorithmic bytes / wall time, GB/s */
+} pkr_stats;
+
+/* Human-readable name of a status code (static string). */
+const char *pkr_status_str(int status);
+
+/* Library version string, e.g. "pkr 0.1 sm_103a". */
+const char *pkr_version(void);
+
+/*
+ * Velocity set and weights of a lattice at expansion order N (host only; no
+ * GPU needed).  Velocities are in the library's order (grouped by symmetry
+ * class).  Any output pointer may be NULL.  vel: 3*Q int32 (x,y,z per
+ * velocity); w, phi, chi: Q doubles.  phi_i, chi_i follow the isotropic
+ * Hermite expansions of order N (Eqs. omega:eq, chi:eq for D=1, N=7 and
+ * omega:eq3, chi:eq3 for D=3, N=5).  Errors: PKR_EINVAL for an unknown
+ * lattice or an order the lattice cannot carry.
+ */
+int pkr_lattice_info(int lattice, int order, int32_t *Q, int32_t *dim, int32_t *vel,
+                     double *w, double *phi, double *chi, double *cs2);
+
+/* tau_lb = 1/2 + Kn * min_k(n_k > 1) / c_s (Kn = lambda / L with the mean free
+ * path lambda = c_s (tau_lb - 1/2); Sec. "From Boltzmann kinetic theory to
+ * diffusion equation").  Host only. */
+int pkr_tau_from_knudsen(int lattice, double knudsen, const int64_t n[3], double *tau_lb);
+
+/* Device bytes a plan for this problem allocates (populations, source, Phi,
+ * scratch).  Host only. */
+int pkr_plan_bytes(const pkr_problem *problem, size_t *bytes);
+
+/* ---------------------------------------------------------------------
+ * Plans: device-resident state of one solve.  A plan owns two population
+ * arrays (Q planes of V sites each, ping-pong), the source S, Phi and a small
+ * scratch area.  All work is queued on the plan's stream.
+ * --------------------------------------------------------------------- */
+typedef struct pkr_plan pkr_plan;
+
+/* Validate the problem, build the lattice tables and allocate device memory
+ * on the current device.  Errors: PKR_EINVAL, PKR_EUNSTABLE (tau_lb at or
+ * below the lattice's stability bound), PKR_ENOMEM, PKR_ECUDA. */
+int pkr_plan_create(const pkr_problem *problem, void *stream, pkr_plan **out);
+
+/* Free everything the plan owns (after synchronising its stream). */
+int pkr_plan_destroy(pkr_plan *plan);
+
+/* Step a0: S = (rho - <rho>) c_s^2 (tau_lb - 1/2) / eps with the mean taken in
+ * binary64 in a fixed order, and reset the populations to zero (t = 0).
+ * rho: V doubles, device pointer (rho_on_host = 0) or host pointer (1).
+ * Synchronises.  Errors: PKR_EINVAL if rho holds NaN or Inf. */
+int pkr_plan_load_source(pkr_plan *plan, const double *rho, int rho_on_host);
+
+/* Advance until Phi^(t + steps) is known, checking the residual every
+ * check_every steps (<= 0: the problem's value) and stopping early once it
+ * drops below tol (tol <= 0: never).  stats may be NULL.  Returns PKR_OK,
+ * PKR_EDIVERGED or PKR_ECUDA.  Synchronises once per check. */
+int pkr_plan_run(pkr_plan *plan, int64_t steps, double tol, int tol_kind, int check_every,
+                 pkr_stats *stats);
+
+/* Queue `count` plain steps (no residual, no synchronisation).  For timing. */
+int pkr_plan_sweeps(pkr_plan *plan, int64_t count);
+
+/* Copy the most recent Phi^t (binary64, V values) into phi: a device pointer
+ * (phi_on_host = 0) or host pointer (1).  Computes it first if the last step
+ * did not.  Synchronises. */
+int pkr_plan_phi(pkr_plan *plan, double *phi, int phi_on_host);
+
+/* Steps t completed so far (Phi^t is the latest density). */
+int64_t pkr_plan_steps(const pkr_plan *plan);
+
+/* Raw access for tests: device pointer of the current population array
+ * (Q*V elements of the storage type, plane i at offset i*V) and of Phi. */
+void *pkr_plan_populations(pkr_plan *plan);
+
+/* ---------------------------------------------------------------------
+ * One-shot solve: create a plan, load rho, run to tol (or max_sweeps), write
+ * Phi, destroy the plan.  rho and phi are device pointers, or host pointers
+ * when host_buffers != 0 (copies then happen inside the call).  Phi is written
+ * on PKR_OK and on PKR_ENOCONV (best effort, stats filled); untouched on
+ * every other error.  With tol <= 0 exactly max_sweeps steps run and the call
+ * returns PKR_OK.
+ * --------------------------------------------------------------------- */
+int pkr_solve(const pkr_problem *problem, const double *rho, double *phi, int host_buffers,
+              pkr_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PKR_H */

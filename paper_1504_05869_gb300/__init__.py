@@ -1,2 +1,142 @@
-"""GB300-native high-order kinetic relaxation Poisson solver (placeholder;
-the C-ABI binding lands with the CUDA library)."""
+"""GB300-native high-order kinetic relaxation Poisson solver.
+
+Thin Python layer over the C ABI of ``include/pkr.h`` (``_pkr``): it only
+fills the ``pkr_problem`` struct and passes pointers.  Device tensors are
+torch CUDA tensors (float64, contiguous); every step of a solve runs in the
+library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _pkr
+from ._pkr import (LATTICE_DIM, LATTICES, PKR_FP32, PKR_FP64, PKR_TOL_MAX_ABS_DPHI,  # noqa: F401
+                   PKR_TOL_REL_L2_DPHI, PkrError, check, pkr_problem, pkr_stats)
+
+PRECISIONS = {"fp64": PKR_FP64, "fp32": PKR_FP32}
+TOL_KINDS = {"max_abs": PKR_TOL_MAX_ABS_DPHI, "rel_l2": PKR_TOL_REL_L2_DPHI}
+
+
+def problem(lattice: str, shape, order: int, tau_lb: float = 0.0, knudsen: float = 0.0,
+            epsilon: float = 1.0, tol: float = 0.0, tol_kind: str = "rel_l2",
+            check_every: int = 32, max_sweeps: int = 1000, precision: str = "fp64"):
+    """pkr_problem for a grid given in numpy/torch order (nz, ny, nx)."""
+    n = list(int(v) for v in tuple(shape)[::-1]) + [1, 1, 1]
+    p = pkr_problem()
+    p.dim = LATTICE_DIM[lattice]
+    p.lattice = LATTICES[lattice]
+    p.n[0], p.n[1], p.n[2] = n[0], n[1], n[2]
+    p.order = int(order)
+    p.precision = PRECISIONS[precision]
+    p.tau_lb = float(tau_lb)
+    p.knudsen = float(knudsen)
+    p.epsilon = float(epsilon)
+    p.tol = float(tol)
+    p.tol_kind = TOL_KINDS[tol_kind]
+    p.check_every = int(check_every)
+    p.max_sweeps = int(max_sweeps)
+    return p
+
+
+def lattice_info(lattice: str, order: int):
+    """(vel (Q,3) int32, w, phi, chi, cs2) from the library's own tables."""
+    import numpy as np
+    Q = ctypes.c_int32()
+    dim = ctypes.c_int32()
+    check(_pkr.pkr_lattice_info(LATTICES[lattice], order, ctypes.byref(Q), ctypes.byref(dim),
+                                None, None, None, None, None), "pkr_lattice_info")
+    q = Q.value
+    vel = np.zeros((q, 3), dtype=np.int32)
+    w, phi, chi = (np.zeros(q) for _ in range(3))
+    cs2 = ctypes.c_double()
+    dp = ctypes.POINTER(ctypes.c_double)
+    check(_pkr.pkr_lattice_info(LATTICES[lattice], order, None, None,
+                                vel.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                w.ctypes.data_as(dp), phi.ctypes.data_as(dp),
+                                chi.ctypes.data_as(dp), ctypes.byref(cs2)), "pkr_lattice_info")
+    return vel, w, phi, chi, cs2.value
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor, or host pointer of a
+    contiguous float64 numpy array / CPU tensor."""
+    if hasattr(t, "data_ptr"):
+        assert t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()
+        return t.data_ptr(), (not t.is_cuda)
+    assert t.dtype.itemsize == 8 and t.flags.c_contiguous
+    return t.ctypes.data, True
+
+
+def solve(rho, phi, prob, stream=None):
+    """pkr_solve: rho and phi both device tensors or both host arrays.
+    Returns (status, stats dict); raises on errors other than PKR_ENOCONV."""
+    rp, rh = _ptr(rho)
+    pp, ph = _ptr(phi)
+    if rh != ph:
+        raise ValueError("rho and phi must both be on the device or both on the host")
+    st = pkr_stats()
+    rc = _pkr.pkr_solve(ctypes.byref(prob), rp, pp, int(rh), ctypes.byref(st),
+                        _stream_ptr(stream))
+    if rc not in (_pkr.PKR_OK, _pkr.PKR_ENOCONV):
+        raise PkrError(rc, "pkr_solve")
+    return rc, st.as_dict()
+
+
+class Plan:
+    """Device-resident solve state (pkr_plan_*)."""
+
+    def __init__(self, prob, stream=None):
+        self.prob = prob
+        self._h = ctypes.c_void_p()
+        check(_pkr.pkr_plan_create(ctypes.byref(prob), _stream_ptr(stream),
+                                   ctypes.byref(self._h)), "pkr_plan_create")
+
+    def load_source(self, rho):
+        p, host = _ptr(rho)
+        check(_pkr.pkr_plan_load_source(self._h, p, int(host)), "pkr_plan_load_source")
+
+    def run(self, steps, tol=0.0, tol_kind="rel_l2", check_every=0):
+        st = pkr_stats()
+        rc = _pkr.pkr_plan_run(self._h, int(steps), float(tol), TOL_KINDS[tol_kind],
+                               int(check_every), ctypes.byref(st))
+        if rc not in (_pkr.PKR_OK, _pkr.PKR_EDIVERGED):
+            raise PkrError(rc, "pkr_plan_run")
+        return rc, st.as_dict()
+
+    def sweeps(self, count):
+        check(_pkr.pkr_plan_sweeps(self._h, int(count)), "pkr_plan_sweeps")
+
+    def phi(self, out):
+        p, host = _ptr(out)
+        check(_pkr.pkr_plan_phi(self._h, p, int(host)), "pkr_plan_phi")
+        return out
+
+    def steps(self) -> int:
+        return int(_pkr.pkr_plan_steps(self._h))
+
+    def populations_ptr(self) -> int:
+        return int(_pkr.pkr_plan_populations(self._h) or 0)
+
+    def close(self):
+        if self._h:
+            _pkr.pkr_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,494 @@
+// pkr_api.cpp -- the C ABI (include/pkr.h): plans, the convergence loop and
+// the one-shot solve.  Host code only; every step of the solve runs in the
+// kernels of pkr_kernels.cu and sweep_*.cu.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pkr_internal.h"
+
+using namespace pkr;
+
+namespace pkr {
+template <class L, typename T> int launch_sweep_t(const SweepArgs&, const void*, int, void*);
+template <class L, typename T> int occupancy_t(int*);
+}  // namespace pkr
+
+#define PKR_CK(call)                                     \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return PKR_ECUDA;         \
+    } while (0)
+
+namespace {
+
+template <class L>
+int dispatch_launch(int prec, const SweepArgs& a, const void* c, int grid, void* st)
+{
+    return prec == PKR_FP64 ? launch_sweep_t<L, double>(a, c, grid, st)
+                            : launch_sweep_t<L, float>(a, c, grid, st);
+}
+template <class L>
+int dispatch_occ(int prec, int* b)
+{
+    return prec == PKR_FP64 ? occupancy_t<L, double>(b) : occupancy_t<L, float>(b);
+}
+
+int threads_of(int lattice)
+{
+    switch (lattice) {
+    case PKR_D2Q81: return 3 * 32;
+    case PKR_D2Q169: return 6 * 32;
+    case PKR_D3Q111: return 4 * 32;
+    default: return 4 * 32;
+    }
+}
+
+int tiles_per_block(int lattice)
+{
+    switch (lattice) {
+    case PKR_D2Q81: case PKR_D2Q169: case PKR_D3Q111: return 1;
+    default: return 4;
+    }
+}
+
+int elem_bytes(int precision) { return precision == PKR_FP64 ? 8 : 4; }
+
+double now_ms()
+{
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int validate(const pkr_problem* p, LatticeInfo* li, double* tau)
+{
+    if (!p) return PKR_EINVAL;
+    if (p->dim < 1 || p->dim > 3) return PKR_EINVAL;
+    if (p->precision != PKR_FP64 && p->precision != PKR_FP32) return PKR_EINVAL;
+    int rc = build_lattice(p->lattice, p->order, li);
+    if (rc != PKR_OK) return rc;
+    if (li->dim != p->dim) return PKR_EINVAL;
+    int64_t V = 1;
+    for (int k = 0; k < 3; ++k) {
+        if (p->n[k] < 1) return PKR_EINVAL;
+        if (k >= p->dim && p->n[k] != 1) return PKR_EINVAL;
+        V *= p->n[k];
+        if (V > (int64_t)0x7fffffff) return PKR_EINVAL;  // flat site index is 32-bit
+    }
+    if (p->max_sweeps < 1) return PKR_EINVAL;
+    if (p->tol_kind != PKR_TOL_MAX_ABS_DPHI && p->tol_kind != PKR_TOL_REL_L2_DPHI) return PKR_EINVAL;
+    if (!(p->epsilon >= 0.0) || !std::isfinite(p->epsilon)) return PKR_EINVAL;
+    double t = p->tau_lb;
+    if (!(t > 0.0)) {
+        if (pkr_tau_from_knudsen(p->lattice, p->knudsen, p->n, &t) != PKR_OK) return PKR_EINVAL;
+    }
+    if (!(t > 0.5) || !std::isfinite(t)) return PKR_EINVAL;
+    *tau = t;
+    return PKR_OK;
+}
+
+}  // namespace
+
+struct pkr_plan {
+    pkr_problem prob;
+    LatticeInfo lat;
+    double tau_lb, omega, scale, rho_mean, last_residual, last_res3[3];
+    cudaStream_t stream;
+    int device, grid, red_blocks, elem, small;
+    int64_t V, launches;
+    void* pop[2];
+    int cur;
+    void* S;
+    double* Phi;
+    double* partials;
+    double* scal;   // [0] mean, [1..3] residual out
+    int* flag;
+    double* host;   // pinned: [0] mean, [1..3] residual, [4] flag (as int)
+    bool loaded;
+    Coefs<double> c64;
+    Coefs<float> c32;
+};
+
+namespace {
+
+int launch_one(pkr_plan* P, int mode, bool zero_in)
+{
+    SweepArgs a{};
+    a.A = P->pop[P->cur];
+    a.B = P->pop[P->cur ^ 1];
+    a.S = P->S;
+    a.Phi = P->Phi;
+    a.partials = P->partials;
+    a.V = P->V;
+    a.nx = (int32_t)P->prob.n[0];
+    a.ny = (int32_t)P->prob.n[1];
+    a.nz = (int32_t)P->prob.n[2];
+    a.ntiles = (int32_t)((P->V + 31) / 32);
+    a.mode = mode;
+    a.zero_in = zero_in ? 1 : 0;
+    a.small = P->small;
+    const void* c = P->prob.precision == PKR_FP64 ? (const void*)&P->c64 : (const void*)&P->c32;
+    int rc = 0;
+    const int pr = P->prob.precision;
+    switch (P->prob.lattice) {
+    case PKR_D1Q5: rc = dispatch_launch<D1Q5>(pr, a, c, P->grid, P->stream); break;
+    case PKR_D1Q9: rc = dispatch_launch<D1Q9>(pr, a, c, P->grid, P->stream); break;
+    case PKR_D1Q13: rc = dispatch_launch<D1Q13>(pr, a, c, P->grid, P->stream); break;
+    case PKR_D2Q25: rc = dispatch_launch<D2Q25>(pr, a, c, P->grid, P->stream); break;
+    case PKR_D2Q81: rc = dispatch_launch<D2Q81>(pr, a, c, P->grid, P->stream); break;
+    case PKR_D2Q169: rc = dispatch_launch<D2Q169>(pr, a, c, P->grid, P->stream); break;
+    case PKR_D3Q19: rc = dispatch_launch<D3Q19>(pr, a, c, P->grid, P->stream); break;
+    case PKR_D3Q111: rc = dispatch_launch<D3Q111>(pr, a, c, P->grid, P->stream); break;
+    default: return PKR_EINVAL;
+    }
+    if (rc != 0) return PKR_ECUDA;
+    P->cur ^= 1;
+    P->launches += 1;
+    if (mode == kCheck) {
+        if (launch_finalize_residual(P->partials, P->grid, P->scal + 1, P->stream) != 0)
+            return PKR_ECUDA;
+    }
+    return PKR_OK;
+}
+
+int occupancy(int lattice, int precision, int* b)
+{
+    switch (lattice) {
+    case PKR_D1Q5: return dispatch_occ<D1Q5>(precision, b);
+    case PKR_D1Q9: return dispatch_occ<D1Q9>(precision, b);
+    case PKR_D1Q13: return dispatch_occ<D1Q13>(precision, b);
+    case PKR_D2Q25: return dispatch_occ<D2Q25>(precision, b);
+    case PKR_D2Q81: return dispatch_occ<D2Q81>(precision, b);
+    case PKR_D2Q169: return dispatch_occ<D2Q169>(precision, b);
+    case PKR_D3Q19: return dispatch_occ<D3Q19>(precision, b);
+    case PKR_D3Q111: return dispatch_occ<D3Q111>(precision, b);
+    }
+    return -1;
+}
+
+size_t plan_bytes(const pkr_problem* p, const LatticeInfo& li, int64_t V, int grid_max)
+{
+    const size_t e = (size_t)elem_bytes(p->precision);
+    size_t b = 2 * (size_t)li.Q * (size_t)V * e;   // ping-pong populations
+    b += (size_t)V * e;                             // S
+    b += (size_t)V * 8;                             // Phi
+    b += (size_t)(3 * grid_max + 4096) * 8 + 64;    // partials + scalars + flag
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pkr_status_str(int s)
+{
+    switch (s) {
+    case PKR_OK: return "ok";
+    case PKR_EINVAL: return "invalid argument";
+    case PKR_ENOMEM: return "out of device memory";
+    case PKR_EUNSTABLE: return "relaxation time in the unstable range of this lattice";
+    case PKR_ENOCONV: return "not converged within max_sweeps";
+    case PKR_EDIVERGED: return "iteration diverged";
+    case PKR_ECUDA: return "CUDA runtime error";
+    case PKR_EBUSY: return "not finished";
+    default: return "unknown status";
+    }
+}
+
+const char* pkr_version(void) { return "pkr 0.1 sm_103a"; }
+
+int pkr_lattice_info(int lattice, int order, int32_t* Q, int32_t* dim, int32_t* vel, double* w,
+                     double* phi, double* chi, double* cs2)
+{
+    LatticeInfo li;
+    int rc = build_lattice(lattice, order, &li);
+    if (rc != PKR_OK) return rc;
+    if (Q) *Q = li.Q;
+    if (dim) *dim = li.dim;
+    for (int i = 0; i < li.Q; ++i) {
+        if (vel) {
+            vel[3 * i + 0] = li.vel[3 * i + 0];
+            vel[3 * i + 1] = li.vel[3 * i + 1];
+            vel[3 * i + 2] = li.vel[3 * i + 2];
+        }
+        if (w) w[i] = li.w[i];
+        if (phi) phi[i] = li.phi[i];
+        if (chi) chi[i] = li.chi[i];
+    }
+    if (cs2) *cs2 = li.cs2;
+    return PKR_OK;
+}
+
+int pkr_tau_from_knudsen(int lattice, double knudsen, const int64_t n[3], double* tau_lb)
+{
+    if (!n || !tau_lb || !(knudsen > 0.0) || !std::isfinite(knudsen)) return PKR_EINVAL;
+    int32_t order = 1;
+    LatticeInfo li;
+    int rc = build_lattice(lattice, order, &li);
+    if (rc != PKR_OK) return rc;
+    int64_t L = 0;
+    for (int k = 0; k < 3; ++k)
+        if (n[k] > 1 && (L == 0 || n[k] < L)) L = n[k];
+    if (L == 0) L = 1;
+    *tau_lb = 0.5 + knudsen * (double)L / std::sqrt(li.cs2);
+    return PKR_OK;
+}
+
+int pkr_plan_bytes(const pkr_problem* p, size_t* bytes)
+{
+    LatticeInfo li;
+    double tau;
+    int rc = validate(p, &li, &tau);
+    if (rc != PKR_OK) return rc;
+    if (!bytes) return PKR_EINVAL;
+    const int64_t V = p->n[0] * p->n[1] * p->n[2];
+    *bytes = plan_bytes(p, li, V, 152 * 32);
+    return PKR_OK;
+}
+
+int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
+{
+    if (!out) return PKR_EINVAL;
+    *out = nullptr;
+    LatticeInfo li;
+    double tau;
+    int rc = validate(p, &li, &tau);
+    if (rc != PKR_OK) return rc;
+    const double omega = 1.0 / tau;
+    if (unstable(li, omega)) return PKR_EUNSTABLE;
+
+    pkr_plan* P = new (std::nothrow) pkr_plan();
+    if (!P) return PKR_ENOMEM;
+    P->prob = *p;
+    if (P->prob.epsilon == 0.0) P->prob.epsilon = 1.0;
+    if (P->prob.check_every <= 0) P->prob.check_every = 32;
+    P->lat = li;
+    P->tau_lb = tau;
+    P->omega = omega;
+    P->scale = li.cs2 * (tau - 0.5) / P->prob.epsilon;
+    P->stream = (cudaStream_t)stream;
+    P->V = p->n[0] * p->n[1] * p->n[2];
+    P->elem = elem_bytes(p->precision);
+    P->small = 0;
+    for (int k = 0; k < li.dim; ++k)
+        if (p->n[k] < li.reach) P->small = 1;
+    P->last_residual = -1.0;
+    // collision coefficients per symmetry class
+    P->c64.om1 = 1.0 - omega;
+    P->c32.om1 = (float)(1.0 - omega);
+    for (int c = 0; c < li.ncls; ++c) {
+        P->c64.wphi[c] = omega * li.cls_phi[c];
+        P->c64.chi[c] = li.cls_chi[c];
+        P->c32.wphi[c] = (float)(omega * li.cls_phi[c]);
+        P->c32.chi[c] = (float)li.cls_chi[c];
+    }
+
+    int dev = 0, nsm = 0, bps = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        occupancy(p->lattice, p->precision, &bps) != 0 || bps < 1) {
+        delete P;
+        return PKR_ECUDA;
+    }
+    P->device = dev;
+    const int64_t ntiles = (P->V + 31) / 32;
+    const int64_t nbt = (ntiles + tiles_per_block(p->lattice) - 1) / tiles_per_block(p->lattice);
+    int64_t grid = (int64_t)nsm * bps;
+    if (grid > nbt) grid = nbt;
+    P->grid = (int)grid;
+    P->red_blocks = nsm * 4;
+
+    const size_t popb = (size_t)li.Q * (size_t)P->V * (size_t)P->elem;
+    size_t freeb = 0, totb = 0;
+    if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) {
+        delete P;
+        return PKR_ECUDA;
+    }
+    if (plan_bytes(p, li, P->V, P->grid) > freeb) {
+        delete P;
+        return PKR_ENOMEM;
+    }
+    const size_t nscratch = (size_t)(3 * P->grid > P->red_blocks ? 3 * P->grid : P->red_blocks);
+    bool ok = cudaMalloc(&P->pop[0], popb) == cudaSuccess &&
+              cudaMalloc(&P->pop[1], popb) == cudaSuccess &&
+              cudaMalloc(&P->S, (size_t)P->V * P->elem) == cudaSuccess &&
+              cudaMalloc((void**)&P->Phi, (size_t)P->V * 8) == cudaSuccess &&
+              cudaMalloc((void**)&P->partials, nscratch * 8) == cudaSuccess &&
+              cudaMalloc((void**)&P->scal, 8 * 8) == cudaSuccess &&
+              cudaMalloc((void**)&P->flag, sizeof(int)) == cudaSuccess &&
+              cudaMallocHost((void**)&P->host, 8 * 8) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        pkr_plan_destroy(P);
+        return PKR_ENOMEM;
+    }
+    *out = P;
+    return PKR_OK;
+}
+
+int pkr_plan_destroy(pkr_plan* P)
+{
+    if (!P) return PKR_OK;
+    if (P->stream || P->pop[0]) cudaStreamSynchronize(P->stream);
+    cudaFree(P->pop[0]);
+    cudaFree(P->pop[1]);
+    cudaFree(P->S);
+    cudaFree(P->Phi);
+    cudaFree(P->partials);
+    cudaFree(P->scal);
+    cudaFree(P->flag);
+    if (P->host) cudaFreeHost(P->host);
+    delete P;
+    return PKR_OK;
+}
+
+int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
+{
+    if (!P || !rho) return PKR_EINVAL;
+    const double* rd = rho;
+    if (rho_on_host) {
+        // stage rho through the Phi buffer (V doubles), which is reset below
+        PKR_CK(cudaMemcpyAsync(P->Phi, rho, (size_t)P->V * 8, cudaMemcpyHostToDevice, P->stream));
+        rd = P->Phi;
+    }
+    PKR_CK(cudaMemsetAsync(P->flag, 0, sizeof(int), P->stream));
+    if (launch_rho_partials(rd, P->V, P->partials, P->red_blocks, P->flag, P->stream) != 0 ||
+        launch_finalize_mean(P->partials, P->red_blocks, P->V, P->scal, P->stream) != 0 ||
+        launch_make_source(rd, P->scal, P->scale, P->V, P->S, P->prob.precision, P->stream) != 0)
+        return PKR_ECUDA;
+    PKR_CK(cudaMemcpyAsync(P->host, P->scal, 8, cudaMemcpyDeviceToHost, P->stream));
+    PKR_CK(cudaMemcpyAsync(P->host + 4, P->flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    PKR_CK(cudaStreamSynchronize(P->stream));
+    int bad = 0;
+    std::memcpy(&bad, P->host + 4, sizeof(int));
+    if (bad) {
+        P->loaded = false;
+        return PKR_EINVAL;
+    }
+    P->rho_mean = P->host[0];
+    // Phi^0 = 0; the first step starts from zero populations
+    PKR_CK(cudaMemsetAsync(P->Phi, 0, (size_t)P->V * 8, P->stream));
+    P->launches = 0;
+    P->cur = 0;
+    P->last_residual = -1.0;
+    int rc = launch_one(P, kWritePhi, true);
+    if (rc != PKR_OK) return rc;
+    P->loaded = true;
+    return PKR_OK;
+}
+
+int pkr_plan_sweeps(pkr_plan* P, int64_t count)
+{
+    if (!P || !P->loaded || count < 0) return PKR_EINVAL;
+    for (int64_t j = 0; j < count; ++j) {
+        int rc = launch_one(P, j == count - 1 ? kWritePhi : kPlain, false);
+        if (rc != PKR_OK) return rc;
+    }
+    return PKR_OK;
+}
+
+int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check_every,
+                 pkr_stats* st)
+{
+    if (!P || !P->loaded || steps < 0) return PKR_EINVAL;
+    if (tol_kind != PKR_TOL_MAX_ABS_DPHI && tol_kind != PKR_TOL_REL_L2_DPHI) return PKR_EINVAL;
+    const int64_t K = check_every > 0 ? check_every : P->prob.check_every;
+    const double t0 = now_ms();
+    int status = PKR_OK;
+    double min_res = INFINITY;
+    int nchecks = 0;
+    int64_t done = 0;
+    for (int64_t j = 0; j < steps; ++j) {
+        const int64_t k = P->launches;  // this launch computes Phi^k
+        int mode = kPlain;
+        if (k % K == 0) mode = kCheck;
+        else if ((k + 1) % K == 0 || j == steps - 1) mode = kWritePhi;
+        int rc = launch_one(P, mode, false);
+        if (rc != PKR_OK) return rc;
+        ++done;
+        if (mode == kCheck) {
+            PKR_CK(cudaMemcpyAsync(P->host + 1, P->scal + 1, 3 * 8, cudaMemcpyDeviceToHost,
+                                   P->stream));
+            PKR_CK(cudaStreamSynchronize(P->stream));
+            const double r = P->host[1 + (tol_kind == PKR_TOL_MAX_ABS_DPHI ? 0 : 1)];
+            P->last_residual = r;
+            ++nchecks;
+            if (!std::isfinite(P->host[1]) || !std::isfinite(P->host[3]) ||
+                (nchecks > 2 && r > 1e6 * min_res && r > 1e-300)) {
+                status = PKR_EDIVERGED;
+                break;
+            }
+            if (r < min_res) min_res = r;
+            if (tol > 0.0 && r < tol) break;
+        }
+    }
+    PKR_CK(cudaStreamSynchronize(P->stream));
+    const double ms = now_ms() - t0;
+    if (st) {
+        st->sweeps = P->launches - 1;
+        st->launches = P->launches;
+        st->residual = P->last_residual;
+        st->rho_mean_removed = P->rho_mean;
+        st->tau_lb = P->tau_lb;
+        st->cs2 = P->lat.cs2;
+        st->wall_ms = ms;
+        const double upd = (double)done * (double)P->V;
+        st->glups = ms > 0 ? upd / (ms * 1e6) : 0.0;
+        const double bytes_site = 2.0 * P->lat.Q * P->elem + P->elem;
+        st->hbm_gbs = ms > 0 ? upd * bytes_site / (ms * 1e6) : 0.0;
+    }
+    return status;
+}
+
+int pkr_plan_phi(pkr_plan* P, double* phi, int phi_on_host)
+{
+    if (!P || !phi || !P->loaded) return PKR_EINVAL;
+    PKR_CK(cudaMemcpyAsync(phi, P->Phi, (size_t)P->V * 8,
+                           phi_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                           P->stream));
+    PKR_CK(cudaStreamSynchronize(P->stream));
+    return PKR_OK;
+}
+
+int64_t pkr_plan_steps(const pkr_plan* P) { return P && P->launches > 0 ? P->launches - 1 : 0; }
+
+void* pkr_plan_populations(pkr_plan* P) { return P ? P->pop[P->cur] : nullptr; }
+
+int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buffers,
+              pkr_stats* st, void* stream)
+{
+    if (!rho || !phi) return PKR_EINVAL;
+    const double t0 = now_ms();
+    pkr_plan* P = nullptr;
+    int rc = pkr_plan_create(p, stream, &P);
+    if (rc != PKR_OK) return rc;
+    rc = pkr_plan_load_source(P, rho, host_buffers);
+    if (rc != PKR_OK) {
+        pkr_plan_destroy(P);
+        return rc;
+    }
+    pkr_stats s{};
+    rc = pkr_plan_run(P, p->max_sweeps, p->tol, p->tol_kind, p->check_every, &s);
+    if (rc == PKR_OK && p->tol > 0.0 && !(s.residual >= 0.0 && s.residual < p->tol))
+        rc = PKR_ENOCONV;
+    if (rc == PKR_OK || rc == PKR_ENOCONV) {
+        int rc2 = pkr_plan_phi(P, phi, host_buffers);
+        if (rc2 != PKR_OK) rc = rc2;
+    }
+    const double ms = now_ms() - t0;
+    if (st) {
+        *st = s;
+        st->wall_ms = ms;
+        const double upd = (double)(P->launches) * (double)P->V;
+        st->glups = ms > 0 ? upd / (ms * 1e6) : 0.0;
+        st->hbm_gbs = ms > 0 ? upd * (2.0 * P->lat.Q * P->elem + P->elem) / (ms * 1e6) : 0.0;
+    }
+    pkr_plan_destroy(P);
+    return rc;
+}
+
+}  // extern "C"

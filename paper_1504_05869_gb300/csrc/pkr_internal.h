@@ -1,0 +1,71 @@
+// pkr_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/pkr.h"
+#include "pkr_lattices.h"
+
+namespace pkr {
+
+constexpr int kMaxQ = 169;
+
+struct LatticeInfo {
+    int lattice, order, Q, dim, reach, ncls;
+    int vel[3 * kMaxQ];
+    int cls[kMaxQ];
+    int key[kMaxQ];
+    long double wl[kMaxQ];
+    double w[kMaxQ], phi[kMaxQ], chi[kMaxQ];
+    double cls_phi[kMaxClasses], cls_chi[kMaxClasses];
+    long double cs2l;
+    double cs2;
+};
+
+int build_lattice(int lattice, int order, LatticeInfo* out);
+bool unstable(const LatticeInfo& li, double omega);
+
+// Per-class coefficients handed to the sweep kernels by value (kernel
+// parameter space, so concurrent plans never share state).
+template <typename R>
+struct Coefs {
+    R om1;                     // 1 - omega
+    R wphi[kMaxClasses];       // omega * phi_c
+    R chi[kMaxClasses];        // chi_c
+};
+
+enum SweepMode { kPlain = 0, kWritePhi = 1, kCheck = 2 };
+
+struct SweepArgs {
+    const void* A;        // populations in (pulled), Q planes of V
+    void* B;              // populations out
+    const void* S;        // source, V values of the storage type
+    double* Phi;          // density buffer (binary64)
+    double* partials;     // residual partials: 3 doubles per block
+    int64_t V;            // sites
+    int32_t nx, ny, nz;
+    int32_t ntiles;       // ceil(V / 32)
+    int32_t mode;         // SweepMode
+    int32_t zero_in;      // populations in are all zero (first step)
+    int32_t small;        // some edge shorter than the lattice reach
+};
+
+// Launch one sweep for (lattice, precision); grid = blocks.  Returns the
+// cudaError_t as int.
+int launch_sweep(int lattice, int precision, const SweepArgs& a, const void* coefs, int grid,
+                 void* stream);
+// Threads per block and blocks per SM the sweep of this lattice uses.
+int sweep_block_threads(int lattice);
+int sweep_occupancy(int lattice, int precision, int* blocks_per_sm);
+
+// Source preparation and reductions (pkr_kernels.cu).
+int launch_rho_partials(const double* rho, int64_t V, double* partials, int nblocks,
+                        int* nonfinite, void* stream);
+int launch_finalize_mean(const double* partials, int nblocks, int64_t V, double* mean,
+                         void* stream);
+int launch_make_source(const double* rho, const double* mean, double scale, int64_t V,
+                       void* S, int precision, void* stream);
+int launch_finalize_residual(const double* partials, int nblocks, double* out3, void* stream);
+
+}  // namespace pkr

@@ -1,0 +1,156 @@
+// pkr_kernels.cu -- source preparation (step a0) and the deterministic
+// binary64 reductions of the solver.
+//
+// Source (text after Eq. poisson1): S = (rho - <rho>) c_s^2 (tau_lb - 1/2)/eps.
+// The mean is a two-pass reduction in a fixed order (per-thread strided sums,
+// a fixed shuffle tree per block, then one block over the block partials), so
+// repeated runs give bit-identical S.
+#include <cuda_runtime.h>
+
+#include "pkr_internal.h"
+
+namespace pkr {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+rho_partials_kernel(const double* __restrict__ rho, int64_t V, double* __restrict__ partials,
+                    int* nonfinite)
+{
+    __shared__ double sm[kRedThreads / 32];
+    double acc = 0.0;
+    int bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += stride) {
+        const double r = rho[i];
+        bad |= !isfinite(r);
+        acc += r;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(nonfinite, 1);
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kRedThreads / 32; ++k) t += sm[k];
+        partials[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+finalize_mean_kernel(const double* __restrict__ partials, int n, int64_t V, double* mean)
+{
+    __shared__ double sm[kRedThreads / 32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += kRedThreads) acc += partials[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kRedThreads / 32; ++k) t += sm[k];
+        *mean = t / (double)V;
+    }
+}
+
+template <typename T>
+__global__ void make_source_kernel(const double* __restrict__ rho, const double* __restrict__ mean,
+                                   double scale, int64_t V, T* __restrict__ S)
+{
+    const double m = *mean;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += stride)
+        S[i] = (T)((rho[i] - m) * scale);
+}
+
+// out3[0] = max |dPhi|, out3[1] = ||dPhi||_2 / ||Phi||_2 (0 if both vanish,
+// +inf if only Phi does), out3[2] = ||Phi||_2.
+__global__ void __launch_bounds__(kRedThreads)
+finalize_residual_kernel(const double* __restrict__ partials, int n, double* out3)
+{
+    __shared__ double s0[kRedThreads / 32], s1[kRedThreads / 32], s2[kRedThreads / 32];
+    double d2 = 0.0, n2 = 0.0, mx = 0.0;
+    for (int i = threadIdx.x; i < n; i += kRedThreads) {
+        d2 += partials[3 * i + 0];
+        n2 += partials[3 * i + 1];
+        mx = fmax(mx, partials[3 * i + 2]);
+    }
+    d2 = warp_sum(d2);
+    n2 = warp_sum(n2);
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) {
+        s0[threadIdx.x >> 5] = d2;
+        s1[threadIdx.x >> 5] = n2;
+        s2[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int k = 0; k < kRedThreads / 32; ++k) {
+            a += s0[k];
+            b += s1[k];
+            c = fmax(c, s2[k]);
+        }
+        out3[0] = c;
+        out3[1] = (b > 0.0) ? sqrt(a) / sqrt(b) : (a == 0.0 ? 0.0 : INFINITY);
+        out3[2] = sqrt(b);
+        // a NaN anywhere poisons the max; report it
+        if (!(a == a) || !(b == b)) {
+            out3[0] = NAN;
+            out3[1] = NAN;
+        }
+    }
+}
+
+}  // namespace
+
+int launch_rho_partials(const double* rho, int64_t V, double* partials, int nblocks,
+                        int* nonfinite, void* stream)
+{
+    rho_partials_kernel<<<nblocks, kRedThreads, 0, (cudaStream_t)stream>>>(rho, V, partials,
+                                                                           nonfinite);
+    return (int)cudaGetLastError();
+}
+
+int launch_finalize_mean(const double* partials, int nblocks, int64_t V, double* mean,
+                         void* stream)
+{
+    finalize_mean_kernel<<<1, kRedThreads, 0, (cudaStream_t)stream>>>(partials, nblocks, V, mean);
+    return (int)cudaGetLastError();
+}
+
+int launch_make_source(const double* rho, const double* mean, double scale, int64_t V, void* S,
+                       int precision, void* stream)
+{
+    int blocks = (int)((V + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (precision == PKR_FP64)
+        make_source_kernel<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(
+            rho, mean, scale, V, static_cast<double*>(S));
+    else
+        make_source_kernel<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(
+            rho, mean, scale, V, static_cast<float*>(S));
+    return (int)cudaGetLastError();
+}
+
+int launch_finalize_residual(const double* partials, int nblocks, double* out3, void* stream)
+{
+    finalize_residual_kernel<<<1, kRedThreads, 0, (cudaStream_t)stream>>>(partials, nblocks, out3);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace pkr

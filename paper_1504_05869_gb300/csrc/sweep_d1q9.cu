@@ -1,0 +1,6 @@
+// Instantiation of the fused sweep for the D1Q9 velocity set.
+#include "pkr_sweep.cuh"
+
+namespace pkr {
+PKR_INSTANTIATE_SWEEP(D1Q9)
+}  // namespace pkr

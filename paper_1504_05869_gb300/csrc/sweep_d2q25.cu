@@ -1,0 +1,6 @@
+// Instantiation of the fused sweep for the D2Q25 velocity set.
+#include "pkr_sweep.cuh"
+
+namespace pkr {
+PKR_INSTANTIATE_SWEEP(D2Q25)
+}  // namespace pkr

@@ -1,0 +1,6 @@
+// Instantiation of the fused sweep for the D3Q19 velocity set.
+#include "pkr_sweep.cuh"
+
+namespace pkr {
+PKR_INSTANTIATE_SWEEP(D3Q19)
+}  // namespace pkr

@@ -38,14 +38,19 @@ class SplitMix64:
         return (self.next_u64() >> 11) * (1.0 / (1 << 53))
 
 
-def _axis_profile(n: int, c: float, sigma: float, half: int):
-    """exp(-d^2/2s^2) along one periodic axis, zero beyond +-half cells."""
-    idx = np.arange(n, dtype=np.float64)
-    d = np.abs(idx - c)
+def _axis_window(n: int, c: float, sigma: float, half: int):
+    """Cells within +-half of c on a periodic axis (each once) and their
+    exp(-d^2 / 2 sigma^2) factors, d the minimum-image distance."""
+    lo = int(math.floor(c)) - half
+    idx = np.arange(lo, lo + 2 * half + 2)
+    if len(idx) >= n:
+        idx = np.arange(n)
+    idx = np.unique(idx % n)
+    d = np.abs(idx.astype(np.float64) - c)
     d = np.minimum(d, n - d)
-    prof = np.exp(-d * d / (2.0 * sigma * sigma))
-    prof[d > half] = 0.0
-    return prof
+    keep = d <= half
+    idx, d = idx[keep], d[keep]
+    return idx, np.exp(-d * d / (2.0 * sigma * sigma))
 
 
 def gaussian_charges(shape, centres, sigmas, charges) -> np.ndarray:
@@ -57,12 +62,12 @@ def gaussian_charges(shape, centres, sigmas, charges) -> np.ndarray:
     for c, s, q in zip(centres, sigmas, charges):
         half = int(math.ceil(10.0 * s))
         norm = q * (2.0 * math.pi * s * s) ** (-dim / 2.0)
-        profs = [_axis_profile(n_xyz[a], c[a], s, half) for a in range(dim)]
+        wins = [_axis_window(n_xyz[a], c[a], s, half) for a in range(dim)]
         # outer product in numpy's (z, y, x) order
-        field = profs[dim - 1]
+        field = wins[dim - 1][1]
         for a in range(dim - 2, -1, -1):
-            field = np.multiply.outer(field, profs[a])
-        rho += norm * field
+            field = np.multiply.outer(field, wins[a][1])
+        rho[np.ix_(*[wins[a][0] for a in range(dim - 1, -1, -1)])] += norm * field
     return rho
 
 

@@ -1,0 +1,132 @@
+"""Host-side checks of the C ABI: the library loads, exports every function
+``include/pkr.h`` declares, and its host logic (lattice tables, Knudsen map,
+argument validation, stability pre-check, memory estimate) agrees with the
+oracle and the paper.  No GPU compute is called here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lattice, tau_from_knudsen
+from oracle.lattice import LATTICES as OR_LATTICES
+from oracle.lattice import MAX_ORDER
+
+import __graft_entry__  # noqa: F401  (puts the repo root on the path)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkr():
+    from paper_1504_05869_gb300 import build
+    build.build()
+    import paper_1504_05869_gb300 as pk
+    pk._pkr.load()
+    return pk
+
+
+def test_exports_every_declared_symbol(pkr):
+    header = open(os.path.join(ROOT, "include", "pkr.h")).read()
+    declared = set(re.findall(r"^\s*[\w\s\*]*?\b(pkr_\w+)\s*\(", header, re.M))
+    declared = {d for d in declared if not d.endswith("_t")}
+    assert declared, "no declarations parsed"
+    lib = ctypes.CDLL(pkr._pkr.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared == set(pkr._pkr.EXPORTS)
+
+
+def test_status_strings(pkr):
+    assert pkr._pkr.pkr_status_str(0) == b"ok"
+    assert b"unstable" in pkr._pkr.pkr_status_str(-3)
+    assert pkr._pkr.pkr_version().startswith(b"pkr")
+
+
+@pytest.mark.parametrize("name,N", [(n, N) for n in OR_LATTICES for N in (1, 3, 5, 7)
+                                    if N <= MAX_ORDER[n]])
+def test_library_tables_match_oracle(pkr, name, N):
+    """The library's hard-coded and computed tables (its own code) agree with
+    the oracle's independently derived ones, velocity by velocity."""
+    vel, w, phi, chi, cs2 = pkr.lattice_info(name, N)
+    lat = lattice(name, N)
+    assert len(w) == lat.Q
+    assert abs(cs2 - lat.cs2) <= 2e-16 * lat.cs2
+    ref = {tuple(v): (a, b, c) for v, a, b, c in zip(lat.vel, lat.w, lat.phi, lat.chi)}
+    assert len({tuple(v) for v in vel}) == lat.Q
+    for v, a, b, c in zip(vel, w, phi, chi):
+        ra, rb, rc = ref[tuple(int(t) for t in v)]
+        assert abs(a - ra) <= 4e-16 * abs(ra)
+        # phi/chi are w_i times a polynomial in xi^2 = |v|^2/c_s^2 whose
+        # terms reach ~xi^6; both sides round those terms differently
+        xi2 = float(np.dot(v, v)) / lat.cs2
+        scale = max(ra * (1.0 + xi2 ** 3), abs(rb), abs(rc))
+        assert abs(b - rb) <= 4e-16 * scale
+        assert abs(c - rc) <= 4e-16 * scale
+
+
+def test_velocities_grouped_by_class(pkr):
+    vel, w, *_ = pkr.lattice_info("D3Q111", 5)
+    keys = [tuple(sorted(np.abs(v))[::-1]) for v in vel]
+    seen = []
+    for k in keys:
+        if not seen or seen[-1] != k:
+            assert k not in seen, "class split"
+            seen.append(k)
+    assert len(seen) == 10
+
+
+def test_tau_from_knudsen_matches_oracle(pkr):
+    for name, n in (("D2Q169", (64, 64, 1)), ("D3Q111", (256, 256, 256)),
+                    ("D3Q19", (48, 32, 40))):
+        for kn in (0.05, 0.1, 0.2, 0.5):
+            arr = (ctypes.c_int64 * 3)(*n)
+            t = ctypes.c_double()
+            assert pkr._pkr.pkr_tau_from_knudsen(pkr.LATTICES[name], kn, arr,
+                                                 ctypes.byref(t)) == 0
+            assert abs(t.value - tau_from_knudsen(kn, n, lattice(name, 1).cs2)) < 1e-12
+
+
+def _create(pkr, **kw):
+    args = dict(lattice="D3Q111", shape=(8, 8, 8), order=5, tau_lb=1.0, max_sweeps=10)
+    args.update(kw)
+    p = pkr.problem(**args)
+    h = ctypes.c_void_p()
+    return pkr._pkr.pkr_plan_create(ctypes.byref(p), None, ctypes.byref(h)), h
+
+
+def test_invalid_problems_rejected_before_any_gpu_work(pkr):
+    assert _create(pkr, order=7)[0] == -1                 # N=7 needs the 13-speed sets
+    assert _create(pkr, tau_lb=0.5)[0] == -1              # tau must exceed 1/2
+    assert _create(pkr, lattice="D2Q169", order=7)[0] == -1   # 2D set on a 3D grid
+    assert _create(pkr, shape=(0, 8, 8))[0] == -1
+    assert _create(pkr, max_sweeps=0)[0] == -1
+    p = pkr.problem("D3Q111", (8, 8, 8), 5, tau_lb=1.0)
+    p.tol_kind = 7
+    h = ctypes.c_void_p()
+    assert pkr._pkr.pkr_plan_create(ctypes.byref(p), None, ctypes.byref(h)) == -1
+
+
+def test_stability_precheck(pkr):
+    """tau_lb = 0.6 on the N=5 3D set has growing modes (the oracle's
+    instability test shows them); the plan is refused with PKR_EUNSTABLE.
+    D3Q19 with N=1 (positive weights) is accepted by the pre-check."""
+    assert _create(pkr, tau_lb=0.6)[0] == -3
+    assert _create(pkr, lattice="D2Q169", shape=(16, 16), order=7, tau_lb=0.7)[0] == -3
+    rc, h = _create(pkr, lattice="D3Q19", order=1, tau_lb=0.6)
+    assert rc in (0, -6)   # passes the pre-check; -6 where no GPU is present
+    if rc == 0:
+        pkr._pkr.pkr_plan_destroy(h)
+
+
+def test_plan_bytes(pkr):
+    p = pkr.problem("D3Q111", (256, 256, 256), 5, tau_lb=1.0)
+    b = ctypes.c_size_t()
+    assert pkr._pkr.pkr_plan_bytes(ctypes.byref(p), ctypes.byref(b)) == 0
+    V = 256 ** 3
+    assert 2 * 111 * V * 8 < b.value < 2 * 111 * V * 8 + 3 * V * 8
+    p32 = pkr.problem("D3Q111", (256, 256, 256), 5, tau_lb=1.0, precision="fp32")
+    b32 = ctypes.c_size_t()
+    assert pkr._pkr.pkr_plan_bytes(ctypes.byref(p32), ctypes.byref(b32)) == 0
+    assert b32.value < 0.55 * b.value

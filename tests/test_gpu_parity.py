@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the oracle.
+
+FP64 bar: relative L2 difference of Phi <= 1e-12 after the same number of
+steps (both sides round differently only in the order of the Q-term density
+sum and in the fused multiply-adds, a few ulps per step, and the scheme is a
+contraction).  FP32 storage is held to 2e-5 (binary32 rounding of each
+population, growing like the step count times 6e-8 and bounded by the
+contraction).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_05869_gb300.workloads import sinusoid, stiff_source
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+    return pk
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def _gpu_solve(pk, rho, lattice, order, tau, steps=None, tol=0.0, tol_kind="rel_l2",
+               check_every=8, precision="fp64", host=False, max_sweeps=None):
+    import torch
+    prob = pk.problem(lattice, rho.shape, order, tau_lb=tau, tol=tol, tol_kind=tol_kind,
+                      check_every=check_every, max_sweeps=max_sweeps or steps,
+                      precision=precision)
+    if host:
+        out = np.empty_like(rho)
+        rc, st = pk.solve(np.ascontiguousarray(rho), out, prob)
+        return out, rc, st
+    r = torch.from_numpy(np.ascontiguousarray(rho)).cuda()
+    phi = torch.empty_like(r)
+    rc, st = pk.solve(r, phi, prob)
+    return phi.cpu().numpy(), rc, st
+
+
+def _rand(shape, seed):
+    r = np.random.default_rng(seed).standard_normal(shape)
+    return r - r.mean()
+
+
+# several tiles of 32 sites, ragged tails, every lattice, edges shorter than
+# the reach (wrap more than once) and the 2D/1D layouts
+CASES = [
+    ("D1Q5", 3, (45,), 0.9),
+    ("D1Q9", 5, (77,), 1.7),
+    ("D1Q13", 7, (100,), 1.0),
+    ("D1Q13", 7, (5,), 1.2),
+    ("D2Q25", 1, (9, 13), 0.8),
+    ("D2Q81", 5, (17, 23), 1.2),
+    ("D2Q169", 7, (21, 19), 6.04398),
+    ("D2Q169", 7, (4, 7), 1.0),
+    ("D3Q19", 1, (7, 9, 11), 0.75),
+    ("D3Q19", 3, (6, 5, 8), 1.1),
+    ("D3Q111", 5, (9, 7, 13), 1.0),
+    ("D3Q111", 5, (16, 16, 16), 2.5),
+    ("D3Q111", 5, (2, 3, 5), 1.4),
+]
+
+
+@pytest.mark.parametrize("lattice,order,shape,tau", CASES)
+def test_fixed_steps_fp64(pk, lattice, order, shape, tau):
+    rho = _rand(shape, 1)
+    for steps in (1, 2, 17):
+        got, rc, st = _gpu_solve(pk, rho, lattice, order, tau, steps=steps)
+        assert rc == 0 and st["sweeps"] == steps
+        ref = oracle.solve(rho, lattice, order, tau_lb=tau, max_steps=steps).phi
+        assert _rel(got, ref) <= FP64_TOL, (steps, _rel(got, ref))
+
+
+@pytest.mark.parametrize("lattice,order,shape,tau,kind,tol", [
+    ("D2Q169", 7, (24, 24), 1.0, "max_abs", 1e-12),
+    ("D3Q111", 5, (12, 10, 14), 1.3, "rel_l2", 1e-10),
+    ("D3Q19", 1, (16, 12, 10), 1.0, "rel_l2", 1e-9),
+])
+def test_converged_solve_matches_oracle(pk, lattice, order, shape, tau, kind, tol):
+    rho, _ = stiff_source(shape, count=6, sigma=1.5, seed=4)
+    kid = 0 if kind == "max_abs" else 1
+    ref = oracle.solve(rho, lattice, order, tau_lb=tau, tol=tol, tol_kind=kid,
+                       check_every=8, max_steps=200000)
+    got, rc, st = _gpu_solve(pk, rho, lattice, order, tau, tol=tol, tol_kind=kind,
+                             check_every=8, max_sweeps=200000)
+    assert rc == 0
+    assert st["sweeps"] == ref.steps
+    assert _rel(got, ref.phi) <= FP64_TOL
+    assert st["residual"] < tol
+    assert abs(st["rho_mean_removed"] - rho.mean()) < 1e-15
+
+
+def test_config_1_geometry(pk):
+    """64x64 sinusoid, D2Q169 N=7, Kn 0.1 (tau_lb from the Knudsen reading),
+    stop at max |dPhi| < 1e-12."""
+    rho = sinusoid((64, 64))
+    lat = oracle.lattice("D2Q169", 7)
+    tau = oracle.tau_from_knudsen(0.1, (64, 64, 1), lat.cs2)
+    ref = oracle.solve(rho, "D2Q169", 7, tau_lb=tau, tol=1e-12, tol_kind=0,
+                       check_every=1, max_steps=100000)
+    # tau_lb from the Knudsen number inside the library
+    import torch
+    prob = pk.problem("D2Q169", (64, 64), 7, knudsen=0.1, tol=1e-12, tol_kind="max_abs",
+                       check_every=1, max_sweeps=100000)
+    r = torch.from_numpy(rho).cuda()
+    phi = torch.empty_like(r)
+    rc2, st2 = pk.solve(r, phi, prob)
+    assert rc2 == 0 and abs(st2["tau_lb"] - tau) < 1e-12
+    assert st2["sweeps"] == ref.steps
+    assert _rel(phi.cpu().numpy(), ref.phi) <= FP64_TOL
+
+
+def test_host_buffers_same_as_device(pk):
+    rho = _rand((10, 12, 9), 3)
+    a, rc1, _ = _gpu_solve(pk, rho, "D3Q111", 5, 1.1, steps=9)
+    b, rc2, _ = _gpu_solve(pk, rho, "D3Q111", 5, 1.1, steps=9, host=True)
+    assert rc1 == 0 and rc2 == 0
+    assert np.array_equal(a, b)
+
+
+def test_deterministic(pk):
+    rho = _rand((20, 18, 16), 5)
+    a, _, s1 = _gpu_solve(pk, rho, "D3Q111", 5, 1.5, tol=1e-9, max_sweeps=5000)
+    b, _, s2 = _gpu_solve(pk, rho, "D3Q111", 5, 1.5, tol=1e-9, max_sweeps=5000)
+    assert np.array_equal(a, b) and s1["residual"] == s2["residual"]
+
+
+@pytest.mark.parametrize("lattice,order,shape,tau", [
+    ("D3Q111", 5, (9, 7, 13), 1.0),
+    ("D2Q169", 7, (21, 19), 1.5),
+    ("D3Q19", 1, (7, 9, 11), 0.8),
+])
+def test_fixed_steps_fp32(pk, lattice, order, shape, tau):
+    rho = _rand(shape, 6)
+    steps = 50
+    got, rc, st = _gpu_solve(pk, rho, lattice, order, tau, steps=steps, precision="fp32")
+    ref = oracle.solve(rho, lattice, order, tau_lb=tau, max_steps=steps).phi
+    assert rc == 0
+    assert _rel(got, ref) < 2e-5
+
+
+def test_nan_source_rejected(pk):
+    rho = _rand((8, 8, 8), 7)
+    rho[3, 4, 5] = np.nan
+    with pytest.raises(pk.PkrError) as e:
+        _gpu_solve(pk, rho, "D3Q111", 5, 1.0, steps=3)
+    assert e.value.status == -1
+
+
+def test_not_converged_still_writes_phi(pk):
+    rho = _rand((8, 8, 8), 8)
+    got, rc, st = _gpu_solve(pk, rho, "D3Q111", 5, 1.0, tol=1e-14, max_sweeps=16)
+    assert rc == -4 and st["sweeps"] == 16
+    ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.0, max_steps=16).phi
+    assert _rel(got, ref) <= FP64_TOL
+
+
+def test_plan_stepping_is_incremental(pk):
+    """run(a) then run(b) equals run(a + b); plain sweeps then a run too."""
+    import torch
+    rho = _rand((11, 9, 10), 9)
+    prob = pk.problem("D3Q111", rho.shape, 5, tau_lb=1.2, max_sweeps=100, check_every=4)
+    r = torch.from_numpy(rho).cuda()
+    out = torch.empty_like(r)
+    with pk.Plan(prob) as P:
+        P.load_source(r)
+        P.run(7)
+        P.sweeps(5)
+        P.run(6)
+        assert P.steps() == 18
+        P.phi(out)
+    ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.2, max_steps=18).phi
+    assert _rel(out.cpu().numpy(), ref) <= FP64_TOL
+
+
+def _impulse_response(lattice, order, tau, steps):
+    lat = oracle.lattice(lattice, order)
+    R = lat.reach * steps
+    m = 2 * R + 1
+    S = np.zeros((m, m, m))
+    S[R, R, R] = 1.0
+    K = oracle.solve(S, lattice, order, tau_lb=tau, max_steps=steps, S=S).phi
+    return K, R
+
+
+@pytest.mark.slow
+def test_full_size_256_sampled(pk):
+    """256^3, 64 Gaussians (sigma 2, seed 0), D3Q111 N=5 at Kn 0.2 in the
+    benchmark's launch configuration.  After 4 steps Phi(x) is the oracle's
+    4-step impulse response convolved with S, evaluated one site at a time."""
+    import torch
+    shape = (256, 256, 256)
+    rho, _ = stiff_source(shape, count=64, sigma=2.0, seed=0)
+    lat = oracle.lattice("D3Q111", 5)
+    tau = oracle.tau_from_knudsen(0.2, (256, 256, 256), lat.cs2)
+    steps = 4
+    got, rc, st = _gpu_solve(pk, rho, "D3Q111", 5, tau, steps=steps)
+    assert rc == 0
+    S, _ = oracle.source(rho, lat, tau)
+    K, R = _impulse_response("D3Q111", 5, tau, steps)
+    rng = np.random.default_rng(12)
+    sites = [tuple(rng.integers(0, 256, 3)) for _ in range(300)]
+    sites += [(0, 0, 0), (255, 255, 255), (0, 255, 128), (255, 0, 1)]
+    off = np.arange(-R, R + 1)
+    scale = np.abs(got).max()
+    diffs = []
+    for (z, y, x) in sites:
+        # Phi(x) = sum_d K(d) S(x - d), K indexed from -R..R
+        window = S[np.ix_((z - off) % 256, (y - off) % 256, (x - off) % 256)]
+        diffs.append(got[z, y, x] - float(np.sum(K * window)))
+    assert np.max(np.abs(diffs)) <= 1e-13 * scale
