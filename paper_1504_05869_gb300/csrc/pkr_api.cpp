@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -14,8 +15,8 @@
 using namespace pkr;
 
 namespace pkr {
-template <class L, typename T> int launch_sweep_t(const SweepArgs&, const void*, int, void*);
-template <class L, typename T> int occupancy_t(int*);
+template <class L, typename T> int launch_sweep_t(int, const SweepArgs&, const void*, int, void*);
+template <class L, typename T> int occupancy_t(int, int*);
 }  // namespace pkr
 
 #define PKR_CK(call)                                     \
@@ -27,34 +28,23 @@ template <class L, typename T> int occupancy_t(int*);
 namespace {
 
 template <class L>
-int dispatch_launch(int prec, const SweepArgs& a, const void* c, int grid, void* st)
+int dispatch_launch(int var, int prec, const SweepArgs& a, const void* c, int grid, void* st)
 {
-    return prec == PKR_FP64 ? launch_sweep_t<L, double>(a, c, grid, st)
-                            : launch_sweep_t<L, float>(a, c, grid, st);
+    return prec == PKR_FP64 ? launch_sweep_t<L, double>(var, a, c, grid, st)
+                            : launch_sweep_t<L, float>(var, a, c, grid, st);
 }
 template <class L>
-int dispatch_occ(int prec, int* b)
+int dispatch_occ(int var, int prec, int* b)
 {
-    return prec == PKR_FP64 ? occupancy_t<L, double>(b) : occupancy_t<L, float>(b);
+    return prec == PKR_FP64 ? occupancy_t<L, double>(var, b) : occupancy_t<L, float>(var, b);
 }
 
-int threads_of(int lattice)
-{
-    switch (lattice) {
-    case PKR_D2Q81: return 3 * 32;
-    case PKR_D2Q169: return 6 * 32;
-    case PKR_D3Q111: return 4 * 32;
-    default: return 4 * 32;
-    }
-}
+// Tiles (of 32 sites) a block works on at a time: two warps, one tile each.
+int tiles_per_block(int) { return 2; }
 
-int tiles_per_block(int lattice)
-{
-    switch (lattice) {
-    case PKR_D2Q81: case PKR_D2Q169: case PKR_D3Q111: return 1;
-    default: return 4;
-    }
-}
+int64_t tiles_of(int, const int64_t n[3]) { return (n[0] * n[1] * n[2] + 31) / 32; }
+
+int default_variant() { return kStaged; }
 
 int elem_bytes(int precision) { return precision == PKR_FP64 ? 8 : 4; }
 
@@ -98,7 +88,8 @@ struct pkr_plan {
     LatticeInfo lat;
     double tau_lb, omega, scale, rho_mean, last_residual, last_res3[3];
     cudaStream_t stream;
-    int device, grid, red_blocks, elem, small;
+    int device, grid, red_blocks, elem, small, variant;
+    int64_t ntiles;
     int64_t V, launches;
     void* pop[2];
     int cur;
@@ -127,22 +118,23 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
     a.nx = (int32_t)P->prob.n[0];
     a.ny = (int32_t)P->prob.n[1];
     a.nz = (int32_t)P->prob.n[2];
-    a.ntiles = (int32_t)((P->V + 31) / 32);
+    a.ntiles = (int32_t)P->ntiles;
     a.mode = mode;
     a.zero_in = zero_in ? 1 : 0;
     a.small = P->small;
     const void* c = P->prob.precision == PKR_FP64 ? (const void*)&P->c64 : (const void*)&P->c32;
     int rc = 0;
     const int pr = P->prob.precision;
+    const int vr = P->variant;
     switch (P->prob.lattice) {
-    case PKR_D1Q5: rc = dispatch_launch<D1Q5>(pr, a, c, P->grid, P->stream); break;
-    case PKR_D1Q9: rc = dispatch_launch<D1Q9>(pr, a, c, P->grid, P->stream); break;
-    case PKR_D1Q13: rc = dispatch_launch<D1Q13>(pr, a, c, P->grid, P->stream); break;
-    case PKR_D2Q25: rc = dispatch_launch<D2Q25>(pr, a, c, P->grid, P->stream); break;
-    case PKR_D2Q81: rc = dispatch_launch<D2Q81>(pr, a, c, P->grid, P->stream); break;
-    case PKR_D2Q169: rc = dispatch_launch<D2Q169>(pr, a, c, P->grid, P->stream); break;
-    case PKR_D3Q19: rc = dispatch_launch<D3Q19>(pr, a, c, P->grid, P->stream); break;
-    case PKR_D3Q111: rc = dispatch_launch<D3Q111>(pr, a, c, P->grid, P->stream); break;
+    case PKR_D1Q5: rc = dispatch_launch<D1Q5>(vr, pr, a, c, P->grid, P->stream); break;
+    case PKR_D1Q9: rc = dispatch_launch<D1Q9>(vr, pr, a, c, P->grid, P->stream); break;
+    case PKR_D1Q13: rc = dispatch_launch<D1Q13>(vr, pr, a, c, P->grid, P->stream); break;
+    case PKR_D2Q25: rc = dispatch_launch<D2Q25>(vr, pr, a, c, P->grid, P->stream); break;
+    case PKR_D2Q81: rc = dispatch_launch<D2Q81>(vr, pr, a, c, P->grid, P->stream); break;
+    case PKR_D2Q169: rc = dispatch_launch<D2Q169>(vr, pr, a, c, P->grid, P->stream); break;
+    case PKR_D3Q19: rc = dispatch_launch<D3Q19>(vr, pr, a, c, P->grid, P->stream); break;
+    case PKR_D3Q111: rc = dispatch_launch<D3Q111>(vr, pr, a, c, P->grid, P->stream); break;
     default: return PKR_EINVAL;
     }
     if (rc != 0) return PKR_ECUDA;
@@ -155,17 +147,17 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
     return PKR_OK;
 }
 
-int occupancy(int lattice, int precision, int* b)
+int occupancy(int variant, int lattice, int precision, int* b)
 {
     switch (lattice) {
-    case PKR_D1Q5: return dispatch_occ<D1Q5>(precision, b);
-    case PKR_D1Q9: return dispatch_occ<D1Q9>(precision, b);
-    case PKR_D1Q13: return dispatch_occ<D1Q13>(precision, b);
-    case PKR_D2Q25: return dispatch_occ<D2Q25>(precision, b);
-    case PKR_D2Q81: return dispatch_occ<D2Q81>(precision, b);
-    case PKR_D2Q169: return dispatch_occ<D2Q169>(precision, b);
-    case PKR_D3Q19: return dispatch_occ<D3Q19>(precision, b);
-    case PKR_D3Q111: return dispatch_occ<D3Q111>(precision, b);
+    case PKR_D1Q5: return dispatch_occ<D1Q5>(variant, precision, b);
+    case PKR_D1Q9: return dispatch_occ<D1Q9>(variant, precision, b);
+    case PKR_D1Q13: return dispatch_occ<D1Q13>(variant, precision, b);
+    case PKR_D2Q25: return dispatch_occ<D2Q25>(variant, precision, b);
+    case PKR_D2Q81: return dispatch_occ<D2Q81>(variant, precision, b);
+    case PKR_D2Q169: return dispatch_occ<D2Q169>(variant, precision, b);
+    case PKR_D3Q19: return dispatch_occ<D3Q19>(variant, precision, b);
+    case PKR_D3Q111: return dispatch_occ<D3Q111>(variant, precision, b);
     }
     return -1;
 }
@@ -287,16 +279,17 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
         P->c32.chi[c] = (float)li.cls_chi[c];
     }
 
+    P->variant = default_variant();
     int dev = 0, nsm = 0, bps = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        occupancy(p->lattice, p->precision, &bps) != 0 || bps < 1) {
+        occupancy(P->variant, p->lattice, p->precision, &bps) != 0 || bps < 1) {
         delete P;
         return PKR_ECUDA;
     }
     P->device = dev;
-    const int64_t ntiles = (P->V + 31) / 32;
-    const int64_t nbt = (ntiles + tiles_per_block(p->lattice) - 1) / tiles_per_block(p->lattice);
+    P->ntiles = tiles_of(P->variant, p->n);
+    const int64_t nbt = (P->ntiles + tiles_per_block(P->variant) - 1) / tiles_per_block(P->variant);
     int64_t grid = (int64_t)nsm * bps;
     if (grid > nbt) grid = nbt;
     P->grid = (int)grid;

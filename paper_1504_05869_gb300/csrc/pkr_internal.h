@@ -36,6 +36,7 @@ struct Coefs {
 };
 
 enum SweepMode { kPlain = 0, kWritePhi = 1, kCheck = 2 };
+enum SweepVariant { kStaged = 0 };
 
 struct SweepArgs {
     const void* A;        // populations in (pulled), Q planes of V
@@ -45,19 +46,12 @@ struct SweepArgs {
     double* partials;     // residual partials: 3 doubles per block
     int64_t V;            // sites
     int32_t nx, ny, nz;
-    int32_t ntiles;       // ceil(V / 32)
+    int32_t ntiles;       // flat tiles of 32 sites
     int32_t mode;         // SweepMode
     int32_t zero_in;      // populations in are all zero (first step)
     int32_t small;        // some edge shorter than the lattice reach
 };
 
-// Launch one sweep for (lattice, precision); grid = blocks.  Returns the
-// cudaError_t as int.
-int launch_sweep(int lattice, int precision, const SweepArgs& a, const void* coefs, int grid,
-                 void* stream);
-// Threads per block and blocks per SM the sweep of this lattice uses.
-int sweep_block_threads(int lattice);
-int sweep_occupancy(int lattice, int precision, int* blocks_per_sm);
 
 // Source preparation and reductions (pkr_kernels.cu).
 int launch_rho_partials(const double* rho, int64_t V, double* partials, int nblocks,

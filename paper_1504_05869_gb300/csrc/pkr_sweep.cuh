@@ -9,13 +9,11 @@
 // emits per-block partial sums of |dPhi|^2, |Phi|^2 and max |dPhi|.
 //
 // Work decomposition.  Sites are taken in the flat order (z*ny + y)*nx + x in
-// tiles of 32 (one warp lane per site).  The Q velocities of a tile are split
-// among G warps (each holds ~Q/G pulled values in registers); the G partial
-// sums of Phi meet in shared memory, then every warp relaxes and stores its
-// own velocities.  A block carries M such tiles.  Blocks are persistent and
-// stride over the tiles.  Every velocity component is a compile-time
-// constant, so the pull address of a velocity is two integer adds on
-// per-tile wrapped row/column offsets.  Plane i of an array lives at i*V.
+// tiles of 32; one warp owns a tile and all Q velocities of it (one lane per
+// site).  Blocks are persistent and stride over the tiles.  Every velocity
+// component is a compile-time constant, so the pull address of a velocity is
+// two integer adds on per-tile wrapped row/column offsets.  Plane i of an
+// array lives at i*V.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -35,12 +33,16 @@ template <class L>
 __host__ __device__ constexpr int cls_of(int i) { return L::T.cls[i]; }
 template <class L>
 __host__ __device__ constexpr int reach_of() { return L::T.reach; }
-
-// Velocity groups per tile (G) and tiles per block (M) of each lattice.
-template <class L> struct Split { static constexpr int G = 1, M = 4; };
-template <> struct Split<D2Q81> { static constexpr int G = 3, M = 1; };
-template <> struct Split<D2Q169> { static constexpr int G = 6, M = 1; };
-template <> struct Split<D3Q111> { static constexpr int G = 4, M = 1; };
+template <class L>
+__host__ __device__ constexpr int ncls_of() { return L::T.ncls; }
+// First velocity of symmetry class c (Q for c = ncls).
+template <class L>
+__host__ __device__ constexpr int cls_begin(int c)
+{
+    for (int i = 0; i < L::Q; ++i)
+        if (L::T.cls[i] == c) return i;
+    return L::Q;
+}
 
 template <int I, int N, typename F>
 __device__ __forceinline__ void static_for(F&& f)
@@ -64,85 +66,131 @@ __device__ __forceinline__ int wrap_any(int c, int n)
     return r < 0 ? r + n : r;
 }
 
-// Exact sum of binary64 values, rounded once.  The values are aligned to
-// the largest exponent E among them in a 128-bit two's-complement integer
-// whose unit is 2^(E - 1139) (64 bits below the unit in the last place of
-// the largest value; anything smaller than that is dropped), added exactly
-// with integer instructions, and the total is converted back to binary64.
-// On this GPU the FP64 pipe issues about two operations per clock per SM, so
-// a density sum of ~28 values per thread costs ~28 pipe slots in binary64
-// but only four here (two conversions, one FMA and one scaling).  Inf/NaN or
-// values all below 2^-895 take the plain binary64 path.
-template <int N>
-__device__ __forceinline__ double exact_sum(const double* v)
-{
-    int emax = 0;
-#pragma unroll
-    for (int k = 0; k < N; ++k) emax = max(emax, (__double2hiint(v[k]) >> 20) & 0x7ff);
-    if (emax == 0x7ff || emax < 128) {
-        double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < N; ++k) s += v[k];
-        return s;
-    }
-    unsigned long long lo = 0ull;
-    long long hi = 0ll;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const unsigned long long bits = (unsigned long long)__double_as_longlong(v[k]);
-        const int e = (int)((bits >> 52) & 0x7ffull);
-        const unsigned long long m =
-            (bits & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
-        const int sh = (e ? e : 1) - emax + 64;   // <= 64
-        const int sl = sh > 0 ? sh : 0;
-        const int sr = sh < 0 ? -sh : 0;
-        const unsigned long long ms = sr < 64 ? (m >> sr) : 0ull;
-        unsigned long long tlo = sl < 64 ? (ms << sl) : 0ull;
-        unsigned long long thi = sl > 0 ? (ms >> (64 - sl)) : 0ull;
-        // two's complement negation of (thi:tlo) when the sign bit is set
-        const unsigned long long neg = bits >> 63;
-        const unsigned long long mask = 0ull - neg;
-        tlo = (tlo ^ mask) + neg;
-        thi = (thi ^ mask) + ((neg && tlo == 0ull) ? 1ull : 0ull);
-        const unsigned long long nlo = lo + tlo;
-        hi += (long long)thi + (nlo < lo ? 1ll : 0ll);
-        lo = nlo;
-    }
-    const double r = fma((double)hi, 18446744073709551616.0, (double)lo);
-    return r * __longlong_as_double((long long)(emax - 116) << 52);
-}
-
-template <int N>
-__device__ __forceinline__ float exact_sum(const float* v)
-{
-    float s = 0.0f;
-#pragma unroll
-    for (int k = 0; k < N; ++k) s += v[k];
-    return s;
-}
-
 __device__ __forceinline__ void store_stream(double* p, double v) { __stcs(p, v); }
 __device__ __forceinline__ void store_stream(float* p, float v) { __stcs(p, v); }
 
+// ---------------------------------------------------------------------------
+// Staged sweep: one warp owns a tile of 32 consecutive sites and all Q
+// velocities.  The Q pulled values of the tile are copied global -> shared
+// with per-lane asynchronous copies (cp.async, zero-fill for lanes past the
+// end and for the first step), so a warp keeps Q x 256 bytes in flight
+// without spending registers on them.  Each lane then reads back only its own
+// column: no block barrier is needed.  The density is the exact sum above;
+// the equilibrium-plus-source term is formed once per symmetry class.
+// ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(src),
+                 "n"(BYTES), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <class L, typename T>
-__global__ void __launch_bounds__(Split<L>::G * Split<L>::M * 32)
-sweep_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
+struct Staged {
+    static constexpr int WARPS = 2;                 // warps per block
+    static constexpr int Q = L::Q;
+    static constexpr size_t smem_bytes() { return (size_t)WARPS * Q * 32 * sizeof(T); }
+};
+
+// Density of one site from its Q pulled values in shared memory (stride 32)
+// without binary64 additions.  The values are aligned to the largest
+// exponent E among them in a 64-bit two's-complement fixed-point sum whose
+// unit is 2^(E - 1075 - GB), i.e. GB guard bits below the last place of the
+// largest value (GB = 63 - 53 - ceil(log2 Q) leaves room for Q terms).  Each
+// term is rounded to that unit (error <= 2^-(GB+1) ulp of the largest value,
+// below the half-ulp that every plain binary64 addition may lose), the sum is
+// exact, and one conversion plus one exact power-of-two scaling return it to
+// binary64.  On this GPU the FP64 pipe issues about two operations per clock
+// per SM, so this costs two of its slots per site instead of Q - 1.  Inf/NaN
+// inputs, or values all below 2^-1011, take the plain binary64 path.
+__host__ __device__ constexpr int ceil_log2(int q)
+{
+    int r = 0;
+    while ((1 << r) < q) ++r;
+    return r;
+}
+
+template <int Q>
+__device__ __forceinline__ double density_fixed(const volatile double* col)
+{
+    constexpr int GB = 63 - 53 - ceil_log2(Q);
+    static_assert(GB >= 1, "too many velocities for the 64-bit density sum");
+    int emax = 0;
+#pragma unroll 8
+    for (int k = 0; k < Q; ++k) emax = max(emax, (__double2hiint(col[k * 32]) >> 20) & 0x7ff);
+    if (emax == 0x7ff || emax < 64) {
+        double s = 0.0;
+        for (int k = 0; k < Q; ++k) s += col[k * 32];
+        return s;
+    }
+    long long a0 = 0, a1 = 0;
+#pragma unroll 2
+    for (int k = 0; k + 1 < Q; k += 2) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const long long b = __double_as_longlong(col[(k + j) * 32]);
+            const int e = (int)((b >> 52) & 0x7ff);
+            const long long m = (b & 0xfffffffffffffll) | (e ? (1ll << 52) : 0ll);
+            const int sh = emax - (e ? e : 1) - GB;        // > 0: shift right
+            const int ls = sh < 0 ? -sh : 0;
+            const int rs = sh > 0 ? sh : 0;
+            long long t = rs < 63 ? (((m << ls) + ((1ll << rs) >> 1)) >> rs) : 0ll;
+            t = b < 0 ? -t : t;
+            if (j == 0) a0 += t; else a1 += t;
+        }
+    }
+    if (Q & 1) {
+        const long long b = __double_as_longlong(col[(Q - 1) * 32]);
+        const int e = (int)((b >> 52) & 0x7ff);
+        const long long m = (b & 0xfffffffffffffll) | (e ? (1ll << 52) : 0ll);
+        const int sh = emax - (e ? e : 1) - GB;
+        const int ls = sh < 0 ? -sh : 0;
+        const int rs = sh > 0 ? sh : 0;
+        long long t = rs < 63 ? (((m << ls) + ((1ll << rs) >> 1)) >> rs) : 0ll;
+        a0 += b < 0 ? -t : t;
+    }
+    return (double)(a0 + a1) * __longlong_as_double((long long)(emax - 52 - GB) << 52);
+}
+
+template <int Q>
+__device__ __forceinline__ float density_fixed(const volatile float* col)
+{
+    // binary32 storage: plain sum in four interleaved partials (fixed order)
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int k = 0; k + 3 < Q; k += 4) {
+        s0 += col[k * 32];
+        s1 += col[(k + 1) * 32];
+        s2 += col[(k + 2) * 32];
+        s3 += col[(k + 3) * 32];
+    }
+#pragma unroll
+    for (int k = Q - Q % 4; k < Q; ++k) s0 += col[k * 32];
+    return (s0 + s1) + (s2 + s3);
+}
+
+template <class L, typename T>
+__global__ void __launch_bounds__(Staged<L, T>::WARPS * 32)
+sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
 {
     using R = typename AccType<T>::type;
     constexpr int Q = L::Q;
-    constexpr int G = Split<L>::G;
-    constexpr int M = Split<L>::M;
+    constexpr int WARPS = Staged<L, T>::WARPS;
     constexpr int RC = reach_of<L>();
     constexpr int W = 2 * RC + 1;
-    constexpr int CH = (Q + G - 1) / G;
-
-    __shared__ R red[2][M][G][32];
-    __shared__ double rpart[M][3];
+    constexpr int NC = ncls_of<L>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double rpart[WARPS][3];
 
     const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const int grp = wid % G;
-    const int sub = wid / G;
+    const int wib = threadIdx.x >> 5;
+    T* col = reinterpret_cast<T*>(smem_raw) + (size_t)wib * Q * 32 + lane;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(col);
     const T* __restrict__ A = static_cast<const T*>(a.A);
     T* __restrict__ B = static_cast<T*>(a.B);
     const T* __restrict__ S = static_cast<const T*>(a.S);
@@ -150,18 +198,15 @@ sweep_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     const int nxy = a.nx * a.ny;
 
     double rd2 = 0.0, rn2 = 0.0, rmx = 0.0;
-    int buf = 0;
-    const int nbt = (a.ntiles + M - 1) / M;
-    for (int bt = blockIdx.x; bt < nbt; bt += gridDim.x, buf ^= 1) {
-        const int tile = bt * M + sub;
+    const int nw = gridDim.x * WARPS;
+    for (int tile = blockIdx.x * WARPS + wib; tile < a.ntiles; tile += nw) {
         const int64_t s64 = (int64_t)tile * 32 + lane;
-        const bool valid = (tile < a.ntiles) && (s64 < V);
+        const bool valid = s64 < V;
         const int s = valid ? (int)s64 : 0;
         const int x = s % a.nx;
         const int r = s / a.nx;
         const int y = r % a.ny;
         const int z = r / a.ny;
-
         int xs[W], yo[W], zo[W];
 #pragma unroll
         for (int d = -RC; d <= RC; ++d) {
@@ -175,51 +220,37 @@ sweep_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
                 zo[d + RC] = wrap_near(z - d, a.nz) * nxy;
             }
         }
-
-        T g[CH];
-        R part = R(0);
-        const bool load = valid && !a.zero_in;
-        static_for<0, G>([&](auto GI) {
-            constexpr int gi = decltype(GI)::value;
-            constexpr int lo = gi * Q / G;
-            constexpr int hi = (gi + 1) * Q / G;
-            if (grp == gi) {
-                static_for<lo, hi>([&](auto I) {
-                    constexpr int i = decltype(I)::value;
-                    constexpr int ox = vx_of<L>(i) + RC;
-                    constexpr int oy = vy_of<L>(i) + RC;
-                    constexpr int oz = vz_of<L>(i) + RC;
-                    T val = T(0);
-                    if (load) val = A[(int64_t)i * V + (zo[oz] + yo[oy] + xs[ox])];
-                    g[i - lo] = val;
-                });
-                part = exact_sum<hi - lo>(g);
-            }
+        const int nbytes = (valid && !a.zero_in) ? (int)sizeof(T) : 0;
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int ox = vx_of<L>(i) + RC;
+            constexpr int oy = vy_of<L>(i) + RC;
+            constexpr int oz = vz_of<L>(i) + RC;
+            const T* src = A + ((int64_t)i * V + (zo[oz] + yo[oy] + xs[ox]));
+            cp_async<sizeof(T)>(sbase + (uint32_t)(i * 32 * sizeof(T)), src, nbytes);
         });
+        cp_async_wait_all();
 
-        red[buf][sub][grp][lane] = part;
-        __syncthreads();
-        R Phi = red[buf][sub][0][lane];
-#pragma unroll
-        for (int k = 1; k < G; ++k) Phi = fma(red[buf][sub][k][lane], R(1), Phi);
+        const volatile T* vcol = col;
+        const R Phi = density_fixed<Q>(vcol);
         const R Sx = valid ? (R)S[s] : R(0);
-
-        static_for<0, G>([&](auto GI) {
-            constexpr int gi = decltype(GI)::value;
-            constexpr int lo = gi * Q / G;
-            constexpr int hi = (gi + 1) * Q / G;
-            if (grp == gi) {
-                static_for<lo, hi>([&](auto I) {
-                    constexpr int i = decltype(I)::value;
-                    constexpr int cl = cls_of<L>(i);
-                    const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
-                    const R p = fma(c.om1, (R)g[i - lo], e);
-                    if (valid) store_stream(&B[(int64_t)i * V + s], (T)p);
-                });
-            }
-        });
-
-        if (a.mode != kPlain && grp == 0 && valid) {
+        if (valid) {
+            // relax and store, one symmetry class at a time (velocities of a
+            // class are contiguous and share phi_c, chi_c)
+            static_for<0, NC>([&](auto CI) {
+                constexpr int cl = decltype(CI)::value;
+                constexpr int i0 = cls_begin<L>(cl);
+                constexpr int i1 = cls_begin<L>(cl + 1);
+                const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
+                T* dst = B + ((int64_t)i0 * V + s);
+#pragma unroll 4
+                for (int i = i0; i < i1; ++i) {
+                    store_stream(dst, (T)fma(c.om1, (R)vcol[i * 32], e));
+                    dst += V;
+                }
+            });
+        }
+        if (a.mode != kPlain && valid) {
             const double ph = (double)Phi;
             if (a.mode == kCheck) {
                 const double d = ph - a.Phi[s];
@@ -229,26 +260,25 @@ sweep_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
             }
             a.Phi[s] = ph;
         }
+        __syncwarp();
     }
 
     if (a.mode == kCheck) {
-        if (grp == 0) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                rd2 += __shfl_down_sync(0xffffffffu, rd2, o);
-                rn2 += __shfl_down_sync(0xffffffffu, rn2, o);
-                rmx = fmax(rmx, __shfl_down_sync(0xffffffffu, rmx, o));
-            }
-            if (lane == 0) {
-                rpart[sub][0] = rd2;
-                rpart[sub][1] = rn2;
-                rpart[sub][2] = rmx;
-            }
+        for (int o = 16; o > 0; o >>= 1) {
+            rd2 += __shfl_down_sync(0xffffffffu, rd2, o);
+            rn2 += __shfl_down_sync(0xffffffffu, rn2, o);
+            rmx = fmax(rmx, __shfl_down_sync(0xffffffffu, rmx, o));
+        }
+        if (lane == 0) {
+            rpart[wib][0] = rd2;
+            rpart[wib][1] = rn2;
+            rpart[wib][2] = rmx;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-            for (int k = 0; k < M; ++k) {
+            for (int k = 0; k < WARPS; ++k) {
                 t0 += rpart[k][0];
                 t1 += rpart[k][1];
                 t2 = fmax(t2, rpart[k][2]);
@@ -261,26 +291,34 @@ sweep_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
 }
 
 template <class L, typename T>
-int launch_sweep_t(const SweepArgs& a, const void* coefs, int grid, void* stream)
+int launch_sweep_t(int variant, const SweepArgs& a, const void* coefs, int grid, void* stream)
 {
     using R = typename AccType<T>::type;
-    constexpr int threads = Split<L>::G * Split<L>::M * 32;
-    sweep_kernel<L, T><<<grid, threads, 0, (cudaStream_t)stream>>>(
-        a, *static_cast<const Coefs<R>*>(coefs));
+    const Coefs<R>& c = *static_cast<const Coefs<R>*>(coefs);
+    (void)variant;
+    constexpr int threads = Staged<L, T>::WARPS * 32;
+    const size_t smem = Staged<L, T>::smem_bytes();
+    sweep_staged_kernel<L, T><<<grid, threads, smem, (cudaStream_t)stream>>>(a, c);
     return (int)cudaGetLastError();
 }
 
 template <class L, typename T>
-int occupancy_t(int* blocks)
+int occupancy_t(int variant, int* blocks)
 {
-    constexpr int threads = Split<L>::G * Split<L>::M * 32;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sweep_kernel<L, T>, threads, 0);
+    (void)variant;
+    constexpr int threads = Staged<L, T>::WARPS * 32;
+    const size_t smem = Staged<L, T>::smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(sweep_staged_kernel<L, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sweep_staged_kernel<L, T>,
+                                                              threads, smem);
 }
 
-#define PKR_INSTANTIATE_SWEEP(L)                                                        \
-    template int launch_sweep_t<L, double>(const SweepArgs&, const void*, int, void*); \
-    template int launch_sweep_t<L, float>(const SweepArgs&, const void*, int, void*);  \
-    template int occupancy_t<L, double>(int*);                                          \
-    template int occupancy_t<L, float>(int*);
+#define PKR_INSTANTIATE_SWEEP(L)                                                             \
+    template int launch_sweep_t<L, double>(int, const SweepArgs&, const void*, int, void*); \
+    template int launch_sweep_t<L, float>(int, const SweepArgs&, const void*, int, void*);  \
+    template int occupancy_t<L, double>(int, int*);                                          \
+    template int occupancy_t<L, float>(int, int*);
 
 }  // namespace pkr
