@@ -10,7 +10,7 @@ GB) are far larger than L2, so no flush is needed between steps.
 
 ``e2e``: the same metric for a complete solve to rel. residual 1e-10 through
 ``pkr_solve`` with host buffers (H2D of rho and D2H of Phi inside the timed
-region).  ``cpu_baseline``: the oracle (serial C) on a 16-plane slab of the same
+region).  ``cpu_baseline``: the oracle (serial C) on a 64-plane slab of the same
 source.  ``--impl reference`` times that oracle alone, as the reference arm.
 
 Multi-GPU: the path does not shard (one grid per GPU, no collectives), so N
@@ -36,7 +36,7 @@ SHAPE = (256, 256, 256)
 LATTICE, ORDER, KN = "D3Q111", 5, 0.2
 PRECISION = "fp64"
 SWEEPS_PER_STEP = 32
-SLAB = 16            # planes of the CPU-baseline sample
+SLAB = 64            # planes of the CPU-baseline sample
 REF_SLAB = 2         # planes per reference-arm step
 METRIC = "GLUPS (site updates/s, 1e9) of the fused sweep"
 WORKLOAD = "poisson3d_256cube_d3q111_n5_fp64_64gauss_sigma2_seed0_kn0.2"
@@ -121,7 +121,7 @@ class ClockSampler:
 
 
 def cpu_baseline(rho, tau):
-    """The oracle (serial C, one core) on a 16-plane slab of the source."""
+    """The oracle (serial C, one core) on a 64-plane slab of the source."""
     import oracle
     slab = np.ascontiguousarray(rho[:SLAB])
     t0 = time.perf_counter()
