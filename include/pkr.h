@@ -177,6 +177,38 @@ void *pkr_plan_populations(pkr_plan *plan);
 int pkr_solve(const pkr_problem *problem, const double *rho, double *phi, int host_buffers,
               pkr_stats *stats, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free residual (the paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory -- code that runs while a
+ * CUDA graph is being captured, runtimes whose device memory all belongs to
+ * their own pool, loops that must not touch the allocator).
+ *
+ * Computes, in binary64 with a fixed reduction order, the same change of Phi
+ * that the solver's stopping rule uses:
+ *     out[0] = max_x |phi_new - phi_old|
+ *     out[1] = ||phi_new - phi_old||_2 / ||phi_new||_2   (0 if both vanish,
+ *              +inf if only phi_new does; NaN if an input holds NaN)
+ *     out[2] = ||phi_new||_2
+ * phi_new, phi_old: device pointers to V doubles each.  out: host pointer to
+ * 3 doubles.  The call queues two kernels on `stream`, copies out[] back and
+ * synchronises the stream.
+ *
+ * Memory: no cudaMalloc, cudaFree or allocating library routine is called.
+ * The scratch (block partials and the three results, 24.6 KB) is a static
+ * device array of the library, held on every GPU that loads the library
+ * until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array and it keeps the last call's contents, so calls that overlap on the
+ * GPU (different streams, no ordering between them) race: order them.
+ *
+ * Errors: PKR_EINVAL for NULL pointers or V outside [1, PKR_NOALLOC_MAX_SITES];
+ * PKR_ECUDA if a CUDA call fails.
+ */
+#define PKR_NOALLOC_MAX_SITES 2147483647LL
+int pkr_residual_noalloc(const double *phi_new, const double *phi_old, int64_t V, double out[3],
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

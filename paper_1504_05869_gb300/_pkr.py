@@ -29,7 +29,7 @@ EXPORTS = [
     "pkr_status_str", "pkr_version", "pkr_lattice_info", "pkr_tau_from_knudsen",
     "pkr_plan_bytes", "pkr_plan_create", "pkr_plan_destroy", "pkr_plan_load_source",
     "pkr_plan_run", "pkr_plan_sweeps", "pkr_plan_phi", "pkr_plan_steps",
-    "pkr_plan_populations", "pkr_solve",
+    "pkr_plan_populations", "pkr_solve", "pkr_residual_noalloc",
 ]
 
 
@@ -77,6 +77,7 @@ _SIGS = {
     "pkr_plan_populations": (_P, [_P]),
     "pkr_solve": (ctypes.c_int, [ctypes.POINTER(pkr_problem), _P, _P, ctypes.c_int,
                                  ctypes.POINTER(pkr_stats), _P]),
+    "pkr_residual_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _D, _P]),
 }
 
 _lib = None
@@ -133,3 +134,4 @@ pkr_plan_phi = _fn("pkr_plan_phi")
 pkr_plan_steps = _fn("pkr_plan_steps")
 pkr_plan_populations = _fn("pkr_plan_populations")
 pkr_solve = _fn("pkr_solve")
+pkr_residual_noalloc = _fn("pkr_residual_noalloc")
