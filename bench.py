@@ -120,6 +120,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def recorded_traffic():
+    """DRAM bytes per sweep launch of the headline workload from the committed
+    ncu summary, or None if the kernel sources changed since it was taken."""
+    import hashlib
+    if (SHAPE, LATTICE, ORDER, PRECISION) != ((256, 256, 256), "D3Q111", 5, "fp64"):
+        return None
+    csrc = os.path.join(ROOT, "paper_1504_05869_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("pkr_sweep.cuh", "pkr_lattices.h", "sweep_d3q111.cu"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "sweep_d3q111_fp64_128cube_traffic.md")).read()
+    except OSError:
+        return None
+    vals = dict(line.split(": ", 1) for line in txt.splitlines()
+                if line.startswith(("traffic_bytes_per_launch_256cube", "source_sha256_16")))
+    if vals.get("source_sha256_16", "").strip() != h.hexdigest()[:16]:
+        return None
+    return float(vals["traffic_bytes_per_launch_256cube"])
+
+
 def cpu_baseline(rho, tau):
     """The oracle (serial C, one core) on a 64-plane slab of the source."""
     import oracle
@@ -276,7 +297,7 @@ def run(args):
             "hbm_gbs": V * bytes_site * sweeps * world / (dev_ms * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "traffic": None, "peak_source": peak_src,
+                         "traffic": recorded_traffic(), "peak_source": peak_src,
                          "kernel": f"sweep_kernel<{LATTICE},"
                                    f"{'double' if PRECISION == 'fp64' else 'float'}>",
                          "algorithmic_bytes_per_launch": V * bytes_site},

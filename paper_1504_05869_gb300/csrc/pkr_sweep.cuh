@@ -115,64 +115,107 @@ __host__ __device__ constexpr int ceil_log2(int q)
     return r;
 }
 
-template <int Q>
-__device__ __forceinline__ double density_fixed(const volatile double* col)
+// Shared-memory loads issued as volatile asm: a batch of them can go out
+// back to back, and the compiler cannot hoist all Q of them into registers.
+__device__ __forceinline__ double lds_f64(uint32_t addr)
 {
-    constexpr int GB = 63 - 53 - ceil_log2(Q);
-    static_assert(GB >= 1, "too many velocities for the 64-bit density sum");
-    int emax = 0;
-#pragma unroll 8
-    for (int k = 0; k < Q; ++k) emax = max(emax, (__double2hiint(col[k * 32]) >> 20) & 0x7ff);
-    if (emax == 0x7ff || emax < 64) {
-        double s = 0.0;
-        for (int k = 0; k < Q; ++k) s += col[k * 32];
-        return s;
-    }
-    long long a0 = 0, a1 = 0;
-#pragma unroll 2
-    for (int k = 0; k + 1 < Q; k += 2) {
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const long long b = __double_as_longlong(col[(k + j) * 32]);
-            const int e = (int)((b >> 52) & 0x7ff);
-            const long long m = (b & 0xfffffffffffffll) | (e ? (1ll << 52) : 0ll);
-            const int sh = emax - (e ? e : 1) - GB;        // > 0: shift right
-            const int ls = sh < 0 ? -sh : 0;
-            const int rs = sh > 0 ? sh : 0;
-            long long t = rs < 63 ? (((m << ls) + ((1ll << rs) >> 1)) >> rs) : 0ll;
-            t = b < 0 ? -t : t;
-            if (j == 0) a0 += t; else a1 += t;
-        }
-    }
-    if (Q & 1) {
-        const long long b = __double_as_longlong(col[(Q - 1) * 32]);
-        const int e = (int)((b >> 52) & 0x7ff);
-        const long long m = (b & 0xfffffffffffffll) | (e ? (1ll << 52) : 0ll);
-        const int sh = emax - (e ? e : 1) - GB;
-        const int ls = sh < 0 ? -sh : 0;
-        const int rs = sh > 0 ? sh : 0;
-        long long t = rs < 63 ? (((m << ls) + ((1ll << rs) >> 1)) >> rs) : 0ll;
-        a0 += b < 0 ? -t : t;
-    }
-    return (double)(a0 + a1) * __longlong_as_double((long long)(emax - 52 - GB) << 52);
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ int lds_hi32(uint32_t addr)
+{
+    int v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr + 4));
+    return v;
+}
+__device__ __forceinline__ float lds_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+
+// One term of the fixed-point density: the value rounded to the unit
+// 2^(emax - 1075 - GB), sign applied.
+template <int GB>
+__device__ __forceinline__ long long fixed_term(double v, int emax)
+{
+    const long long b = __double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const long long m = e ? (((b & 0xfffffffffffffll) | (1ll << 52)) << GB) : 0ll;
+    const int rs = emax - e;
+    const long long t = rs < 63 ? ((m + ((1ll << rs) >> 1)) >> rs) : 0ll;
+    return b < 0 ? -t : t;
 }
 
 template <int Q>
-__device__ __forceinline__ float density_fixed(const volatile float* col)
+__device__ __forceinline__ double density_fixed(uint32_t col)   // col: shared address, stride 256 B
+{
+    constexpr int GB = 63 - 53 - ceil_log2(Q);
+    constexpr int U = 8;
+    static_assert(GB >= 1, "too many velocities for the 64-bit density sum");
+    // largest exponent: max of the high words with the sign cleared
+    int h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+#pragma unroll 2
+    for (int k = 0; k + 3 < Q; k += 4) {
+        h0 = max(h0, lds_hi32(col + (k + 0) * 256) & 0x7fffffff);
+        h1 = max(h1, lds_hi32(col + (k + 1) * 256) & 0x7fffffff);
+        h2 = max(h2, lds_hi32(col + (k + 2) * 256) & 0x7fffffff);
+        h3 = max(h3, lds_hi32(col + (k + 3) * 256) & 0x7fffffff);
+    }
+#pragma unroll
+    for (int k = Q - Q % 4; k < Q; ++k) h0 = max(h0, lds_hi32(col + k * 256) & 0x7fffffff);
+    const int emax = max(max(h0, h1), max(h2, h3)) >> 20;
+    if (emax == 0x7ff || emax < 64) {
+        double s = 0.0;
+        for (int k = 0; k < Q; ++k) s += lds_f64(col + k * 256);
+        return s;
+    }
+    long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int k = 0; k + U - 1 < Q; k += U) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = lds_f64(col + (k + u) * 256);
+        a0 += fixed_term<GB>(v[0], emax) + fixed_term<GB>(v[4], emax);
+        a1 += fixed_term<GB>(v[1], emax) + fixed_term<GB>(v[5], emax);
+        a2 += fixed_term<GB>(v[2], emax) + fixed_term<GB>(v[6], emax);
+        a3 += fixed_term<GB>(v[3], emax) + fixed_term<GB>(v[7], emax);
+    }
+#pragma unroll
+    for (int k = Q - Q % U; k < Q; ++k) a0 += fixed_term<GB>(lds_f64(col + k * 256), emax);
+    return (double)((a0 + a1) + (a2 + a3)) *
+           __longlong_as_double((long long)(emax - 52 - GB) << 52);
+}
+
+template <int Q>
+__device__ __forceinline__ float density_fixed_f32(uint32_t col)   // stride 128 B
 {
     // binary32 storage: plain sum in four interleaved partials (fixed order)
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
+#pragma unroll 2
     for (int k = 0; k + 3 < Q; k += 4) {
-        s0 += col[k * 32];
-        s1 += col[(k + 1) * 32];
-        s2 += col[(k + 2) * 32];
-        s3 += col[(k + 3) * 32];
+        s0 += lds_f32(col + (k + 0) * 128);
+        s1 += lds_f32(col + (k + 1) * 128);
+        s2 += lds_f32(col + (k + 2) * 128);
+        s3 += lds_f32(col + (k + 3) * 128);
     }
 #pragma unroll
-    for (int k = Q - Q % 4; k < Q; ++k) s0 += col[k * 32];
+    for (int k = Q - Q % 4; k < Q; ++k) s0 += lds_f32(col + k * 128);
     return (s0 + s1) + (s2 + s3);
 }
+
+template <typename T> __device__ __forceinline__ T lds_val(uint32_t addr);
+template <> __device__ __forceinline__ double lds_val<double>(uint32_t addr) { return lds_f64(addr); }
+template <> __device__ __forceinline__ float lds_val<float>(uint32_t addr) { return lds_f32(addr); }
+
+template <int Q, typename T> struct Density;
+template <int Q> struct Density<Q, double> {
+    static __device__ __forceinline__ double run(uint32_t col) { return density_fixed<Q>(col); }
+};
+template <int Q> struct Density<Q, float> {
+    static __device__ __forceinline__ float run(uint32_t col) { return density_fixed_f32<Q>(col); }
+};
 
 template <class L, typename T>
 __global__ void __launch_bounds__(Staged<L, T>::WARPS * 32)
@@ -231,8 +274,7 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
         });
         cp_async_wait_all();
 
-        const volatile T* vcol = col;
-        const R Phi = density_fixed<Q>(vcol);
+        const R Phi = Density<Q, T>::run(sbase);
         const R Sx = valid ? (R)S[s] : R(0);
         if (valid) {
             // relax and store, one symmetry class at a time (velocities of a
@@ -243,9 +285,20 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
                 constexpr int i1 = cls_begin<L>(cl + 1);
                 const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
                 T* dst = B + ((int64_t)i0 * V + s);
-#pragma unroll 4
-                for (int i = i0; i < i1; ++i) {
-                    store_stream(dst, (T)fma(c.om1, (R)vcol[i * 32], e));
+                int i = i0;
+                for (; i + 3 < i1; i += 4) {
+                    const R g0 = lds_val<T>(sbase + (i + 0) * 32 * sizeof(T));
+                    const R g1 = lds_val<T>(sbase + (i + 1) * 32 * sizeof(T));
+                    const R g2 = lds_val<T>(sbase + (i + 2) * 32 * sizeof(T));
+                    const R g3 = lds_val<T>(sbase + (i + 3) * 32 * sizeof(T));
+                    store_stream(dst, (T)fma(c.om1, g0, e));
+                    store_stream(dst + V, (T)fma(c.om1, g1, e));
+                    store_stream(dst + 2 * V, (T)fma(c.om1, g2, e));
+                    store_stream(dst + 3 * V, (T)fma(c.om1, g3, e));
+                    dst += 4 * V;
+                }
+                for (; i < i1; ++i) {
+                    store_stream(dst, (T)fma(c.om1, (R)lds_val<T>(sbase + i * 32 * sizeof(T)), e));
                     dst += V;
                 }
             });
