@@ -214,6 +214,7 @@ def run(args):
         rc, st = plan.run(SWEEPS_PER_STEP)
         return st
 
+    variant, tuned_ms = plan.autotune(2)
     for _ in range(args.warmup):
         st = step()
     tau = st["tau_lb"]
@@ -292,6 +293,7 @@ def run(args):
             "config": {"workload": WORKLOAD, "grid": list(SHAPE), "lattice": LATTICE,
                        "order": ORDER, "knudsen": KN, "tau_lb": tau,
                        "sweeps_per_step": SWEEPS_PER_STEP, "residual_check": "rel_l2 fp64",
+                       "kernel_variant": variant,
                        "l2": "inputs larger than L2 (2 x 14.9 GB populations)",
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs": V * bytes_site * sweeps * world / (dev_ms * 1e-3) / 1e9,

@@ -82,6 +82,9 @@ typedef struct pkr_problem {
     int32_t tol_kind;     /* pkr_tol_kind */
     int32_t check_every;  /* steps between residual checks (<= 0: 32) */
     int64_t max_sweeps;   /* upper bound on the steps taken (>= 1) */
+    int32_t variant;      /* sweep kernel geometry: -1 = library default, 0 .. count-1 =
+                             a compiled variant (pkr_variant_count); all variants give
+                             identical results, they differ only in speed */
 } pkr_problem;
 
 typedef struct pkr_stats {
@@ -119,6 +122,10 @@ int pkr_lattice_info(int lattice, int order, int32_t *Q, int32_t *dim, int32_t *
  * diffusion equation").  Host only. */
 int pkr_tau_from_knudsen(int lattice, double knudsen, const int64_t n[3], double *tau_lb);
 
+/* Number of compiled sweep-kernel geometries for a lattice (velocity groups
+ * per 32-site tile x tiles per block).  Host only; < 0 for an unknown lattice. */
+int pkr_variant_count(int lattice);
+
 /* Device bytes a plan for this problem allocates (populations, source, Phi,
  * scratch).  Host only. */
 int pkr_plan_bytes(const pkr_problem *problem, size_t *bytes);
@@ -150,6 +157,15 @@ int pkr_plan_load_source(pkr_plan *plan, const double *rho, int rho_on_host);
  * PKR_EDIVERGED or PKR_ECUDA.  Synchronises once per check. */
 int pkr_plan_run(pkr_plan *plan, int64_t steps, double tol, int tol_kind, int check_every,
                  pkr_stats *stats);
+
+/* Autotuner: time every compiled sweep variant on the plan's own buffers
+ * (one warm-up step, then `steps_per_variant` timed steps each, CUDA events on
+ * the plan's stream) and keep the fastest.  The steps are real steps of the
+ * solve: the plan advances by (1 + steps_per_variant) x count steps.  Must
+ * follow pkr_plan_load_source.  best_variant / best_ms_per_step may be NULL.
+ * Synchronises. */
+int pkr_plan_autotune(pkr_plan *plan, int steps_per_variant, int32_t *best_variant,
+                      double *best_ms_per_step);
 
 /* Queue `count` plain steps (no residual, no synchronisation).  For timing. */
 int pkr_plan_sweeps(pkr_plan *plan, int64_t count);

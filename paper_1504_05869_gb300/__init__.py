@@ -19,7 +19,8 @@ TOL_KINDS = {"max_abs": PKR_TOL_MAX_ABS_DPHI, "rel_l2": PKR_TOL_REL_L2_DPHI}
 
 def problem(lattice: str, shape, order: int, tau_lb: float = 0.0, knudsen: float = 0.0,
             epsilon: float = 1.0, tol: float = 0.0, tol_kind: str = "rel_l2",
-            check_every: int = 32, max_sweeps: int = 1000, precision: str = "fp64"):
+            check_every: int = 32, max_sweeps: int = 1000, precision: str = "fp64",
+            variant: int = -1):
     """pkr_problem for a grid given in numpy/torch order (nz, ny, nx)."""
     n = list(int(v) for v in tuple(shape)[::-1]) + [1, 1, 1]
     p = pkr_problem()
@@ -35,6 +36,7 @@ def problem(lattice: str, shape, order: int, tau_lb: float = 0.0, knudsen: float
     p.tol_kind = TOL_KINDS[tol_kind]
     p.check_every = int(check_every)
     p.max_sweeps = int(max_sweeps)
+    p.variant = int(variant)
     return p
 
 
@@ -109,6 +111,13 @@ class Plan:
         if rc not in (_pkr.PKR_OK, _pkr.PKR_EDIVERGED):
             raise PkrError(rc, "pkr_plan_run")
         return rc, st.as_dict()
+
+    def autotune(self, steps_per_variant=4):
+        best = ctypes.c_int32()
+        ms = ctypes.c_double()
+        check(_pkr.pkr_plan_autotune(self._h, int(steps_per_variant), ctypes.byref(best),
+                                     ctypes.byref(ms)), "pkr_plan_autotune")
+        return best.value, ms.value
 
     def sweeps(self, count):
         check(_pkr.pkr_plan_sweeps(self._h, int(count)), "pkr_plan_sweeps")

@@ -29,7 +29,8 @@ EXPORTS = [
     "pkr_status_str", "pkr_version", "pkr_lattice_info", "pkr_tau_from_knudsen",
     "pkr_plan_bytes", "pkr_plan_create", "pkr_plan_destroy", "pkr_plan_load_source",
     "pkr_plan_run", "pkr_plan_sweeps", "pkr_plan_phi", "pkr_plan_steps",
-    "pkr_plan_populations", "pkr_solve", "pkr_residual_noalloc",
+    "pkr_plan_populations", "pkr_solve", "pkr_residual_noalloc", "pkr_variant_count",
+    "pkr_plan_autotune",
 ]
 
 
@@ -39,7 +40,8 @@ class pkr_problem(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("tau_lb", ctypes.c_double),
                 ("knudsen", ctypes.c_double), ("epsilon", ctypes.c_double),
                 ("tol", ctypes.c_double), ("tol_kind", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("max_sweeps", ctypes.c_int64)]
+                ("check_every", ctypes.c_int32), ("max_sweeps", ctypes.c_int64),
+                ("variant", ctypes.c_int32)]
 
 
 class pkr_stats(ctypes.Structure):
@@ -78,6 +80,8 @@ _SIGS = {
     "pkr_solve": (ctypes.c_int, [ctypes.POINTER(pkr_problem), _P, _P, ctypes.c_int,
                                  ctypes.POINTER(pkr_stats), _P]),
     "pkr_residual_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _D, _P]),
+    "pkr_variant_count": (ctypes.c_int, [ctypes.c_int]),
+    "pkr_plan_autotune": (ctypes.c_int, [_P, ctypes.c_int, _I32, _D]),
 }
 
 _lib = None
@@ -135,3 +139,5 @@ pkr_plan_steps = _fn("pkr_plan_steps")
 pkr_plan_populations = _fn("pkr_plan_populations")
 pkr_solve = _fn("pkr_solve")
 pkr_residual_noalloc = _fn("pkr_residual_noalloc")
+pkr_variant_count = _fn("pkr_variant_count")
+pkr_plan_autotune = _fn("pkr_plan_autotune")

@@ -16,7 +16,8 @@ using namespace pkr;
 
 namespace pkr {
 template <class L, typename T> int launch_sweep_t(int, const SweepArgs&, const void*, int, void*);
-template <class L, typename T> int occupancy_t(int, int*);
+template <class L, typename T> int occupancy_t(int, int*, int*);
+template <class L> int variant_count_t();
 }  // namespace pkr
 
 #define PKR_CK(call)                                     \
@@ -34,17 +35,38 @@ int dispatch_launch(int var, int prec, const SweepArgs& a, const void* c, int gr
                             : launch_sweep_t<L, float>(var, a, c, grid, st);
 }
 template <class L>
-int dispatch_occ(int var, int prec, int* b)
+int dispatch_occ(int var, int prec, int* b, int* tpb)
 {
-    return prec == PKR_FP64 ? occupancy_t<L, double>(var, b) : occupancy_t<L, float>(var, b);
+    return prec == PKR_FP64 ? occupancy_t<L, double>(var, b, tpb)
+                            : occupancy_t<L, float>(var, b, tpb);
 }
 
-// Tiles (of 32 sites) a block works on at a time: two warps, one tile each.
-int tiles_per_block(int) { return 2; }
+int64_t tiles_of(const int64_t n[3]) { return (n[0] * n[1] * n[2] + 31) / 32; }
 
-int64_t tiles_of(int, const int64_t n[3]) { return (n[0] * n[1] * n[2] + 31) / 32; }
+int variant_count(int lattice)
+{
+    switch (lattice) {
+    case PKR_D1Q5: return variant_count_t<D1Q5>();
+    case PKR_D1Q9: return variant_count_t<D1Q9>();
+    case PKR_D1Q13: return variant_count_t<D1Q13>();
+    case PKR_D2Q25: return variant_count_t<D2Q25>();
+    case PKR_D2Q81: return variant_count_t<D2Q81>();
+    case PKR_D2Q169: return variant_count_t<D2Q169>();
+    case PKR_D3Q19: return variant_count_t<D3Q19>();
+    case PKR_D3Q111: return variant_count_t<D3Q111>();
+    }
+    return -1;
+}
 
-int default_variant() { return kStaged; }
+// Default geometry per (lattice, storage), from autotuning runs on GB300
+// (256^3 D3Q111, 256^3 D3Q19); index into the lattice's variant list
+// {(G,TILES)} = {(1,2),(2,1),(2,2),(3,1),(3,2),(4,1)} for Q > 64, else
+// {(1,2),(1,4)}.
+int default_variant(int lattice, int precision)
+{
+    if (variant_count(lattice) > 2) return precision == PKR_FP64 ? 3 : 0;
+    return 0;
+}
 
 int elem_bytes(int precision) { return precision == PKR_FP64 ? 8 : 4; }
 
@@ -70,6 +92,7 @@ int validate(const pkr_problem* p, LatticeInfo* li, double* tau)
         if (V > (int64_t)0x7fffffff) return PKR_EINVAL;  // flat site index is 32-bit
     }
     if (p->max_sweeps < 1) return PKR_EINVAL;
+    if (p->variant < -1) return PKR_EINVAL;
     if (p->tol_kind != PKR_TOL_MAX_ABS_DPHI && p->tol_kind != PKR_TOL_REL_L2_DPHI) return PKR_EINVAL;
     if (!(p->epsilon >= 0.0) || !std::isfinite(p->epsilon)) return PKR_EINVAL;
     double t = p->tau_lb;
@@ -83,12 +106,15 @@ int validate(const pkr_problem* p, LatticeInfo* li, double* tau)
 
 }  // namespace
 
+// Upper bound on a persistent sweep grid (blocks); sizes the partials scratch.
+constexpr int kMaxGridBlocks = 152 * 32;
+
 struct pkr_plan {
     pkr_problem prob;
     LatticeInfo lat;
     double tau_lb, omega, scale, rho_mean, last_residual, last_res3[3];
     cudaStream_t stream;
-    int device, grid, red_blocks, elem, small, variant;
+    int device, grid, red_blocks, elem, small, variant, nsm;
     int64_t ntiles;
     int64_t V, launches;
     void* pop[2];
@@ -147,19 +173,36 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
     return PKR_OK;
 }
 
-int occupancy(int variant, int lattice, int precision, int* b)
+int occupancy(int variant, int lattice, int precision, int* b, int* tpb)
 {
     switch (lattice) {
-    case PKR_D1Q5: return dispatch_occ<D1Q5>(variant, precision, b);
-    case PKR_D1Q9: return dispatch_occ<D1Q9>(variant, precision, b);
-    case PKR_D1Q13: return dispatch_occ<D1Q13>(variant, precision, b);
-    case PKR_D2Q25: return dispatch_occ<D2Q25>(variant, precision, b);
-    case PKR_D2Q81: return dispatch_occ<D2Q81>(variant, precision, b);
-    case PKR_D2Q169: return dispatch_occ<D2Q169>(variant, precision, b);
-    case PKR_D3Q19: return dispatch_occ<D3Q19>(variant, precision, b);
-    case PKR_D3Q111: return dispatch_occ<D3Q111>(variant, precision, b);
+    case PKR_D1Q5: return dispatch_occ<D1Q5>(variant, precision, b, tpb);
+    case PKR_D1Q9: return dispatch_occ<D1Q9>(variant, precision, b, tpb);
+    case PKR_D1Q13: return dispatch_occ<D1Q13>(variant, precision, b, tpb);
+    case PKR_D2Q25: return dispatch_occ<D2Q25>(variant, precision, b, tpb);
+    case PKR_D2Q81: return dispatch_occ<D2Q81>(variant, precision, b, tpb);
+    case PKR_D2Q169: return dispatch_occ<D2Q169>(variant, precision, b, tpb);
+    case PKR_D3Q19: return dispatch_occ<D3Q19>(variant, precision, b, tpb);
+    case PKR_D3Q111: return dispatch_occ<D3Q111>(variant, precision, b, tpb);
     }
     return -1;
+}
+
+// Select a variant: occupancy, persistent grid size (blocks resident on all
+// SMs, capped by the work).  The partials scratch holds 3 doubles per block
+// of the largest grid any variant may use (allocated at plan creation).
+int set_variant(pkr_plan* P, int variant)
+{
+    int bps = 0, tpb = 1;
+    if (occupancy(variant, P->prob.lattice, P->prob.precision, &bps, &tpb) != 0 || bps < 1)
+        return PKR_ECUDA;
+    const int64_t nbt = (P->ntiles + tpb - 1) / tpb;
+    int64_t grid = (int64_t)P->nsm * bps;
+    if (grid > nbt) grid = nbt;
+    if (grid > kMaxGridBlocks) grid = kMaxGridBlocks;
+    P->variant = variant;
+    P->grid = (int)grid;
+    return PKR_OK;
 }
 
 size_t plan_bytes(const pkr_problem* p, const LatticeInfo& li, int64_t V, int grid_max)
@@ -238,7 +281,7 @@ int pkr_plan_bytes(const pkr_problem* p, size_t* bytes)
     if (rc != PKR_OK) return rc;
     if (!bytes) return PKR_EINVAL;
     const int64_t V = p->n[0] * p->n[1] * p->n[2];
-    *bytes = plan_bytes(p, li, V, 152 * 32);
+    *bytes = plan_bytes(p, li, V, kMaxGridBlocks);
     return PKR_OK;
 }
 
@@ -279,20 +322,25 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
         P->c32.chi[c] = (float)li.cls_chi[c];
     }
 
-    P->variant = default_variant();
-    int dev = 0, nsm = 0, bps = 0;
+    int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        occupancy(P->variant, p->lattice, p->precision, &bps) != 0 || bps < 1) {
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete P;
         return PKR_ECUDA;
     }
     P->device = dev;
-    P->ntiles = tiles_of(P->variant, p->n);
-    const int64_t nbt = (P->ntiles + tiles_per_block(P->variant) - 1) / tiles_per_block(P->variant);
-    int64_t grid = (int64_t)nsm * bps;
-    if (grid > nbt) grid = nbt;
-    P->grid = (int)grid;
+    P->nsm = nsm;
+    P->ntiles = tiles_of(p->n);
+    const int nvar = variant_count(p->lattice);
+    const int var = (p->variant >= 0) ? p->variant : default_variant(p->lattice, p->precision);
+    if (var >= nvar) {
+        delete P;
+        return PKR_EINVAL;
+    }
+    if (set_variant(P, var) != PKR_OK) {
+        delete P;
+        return PKR_ECUDA;
+    }
     P->red_blocks = nsm * 4;
 
     const size_t popb = (size_t)li.Q * (size_t)P->V * (size_t)P->elem;
@@ -301,11 +349,11 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
         delete P;
         return PKR_ECUDA;
     }
-    if (plan_bytes(p, li, P->V, P->grid) > freeb) {
+    if (plan_bytes(p, li, P->V, kMaxGridBlocks) > freeb) {
         delete P;
         return PKR_ENOMEM;
     }
-    const size_t nscratch = (size_t)(3 * P->grid > P->red_blocks ? 3 * P->grid : P->red_blocks);
+    const size_t nscratch = (size_t)3 * kMaxGridBlocks;
     bool ok = cudaMalloc(&P->pop[0], popb) == cudaSuccess &&
               cudaMalloc(&P->pop[1], popb) == cudaSuccess &&
               cudaMalloc(&P->S, (size_t)P->V * P->elem) == cudaSuccess &&
@@ -371,6 +419,47 @@ int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
     int rc = launch_one(P, kWritePhi, true);
     if (rc != PKR_OK) return rc;
     P->loaded = true;
+    return PKR_OK;
+}
+
+int pkr_variant_count(int lattice) { return variant_count(lattice); }
+
+int pkr_plan_autotune(pkr_plan* P, int steps_per_variant, int32_t* best_variant,
+                      double* best_ms_per_step)
+{
+    if (!P || !P->loaded || steps_per_variant < 1) return PKR_EINVAL;
+    const int n = variant_count(P->prob.lattice);
+    cudaEvent_t e0, e1;
+    PKR_CK(cudaEventCreate(&e0));
+    PKR_CK(cudaEventCreate(&e1));
+    int best = P->variant;
+    float best_ms = 1e30f;
+    int rc = PKR_OK;
+    for (int v = 0; v < n && rc == PKR_OK; ++v) {
+        if ((rc = set_variant(P, v)) != PKR_OK) break;
+        if ((rc = launch_one(P, kPlain, false)) != PKR_OK) break;   // warm-up
+        cudaEventRecord(e0, P->stream);
+        for (int k = 0; k < steps_per_variant && rc == PKR_OK; ++k)
+            rc = launch_one(P, kPlain, false);
+        cudaEventRecord(e1, P->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = PKR_ECUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)steps_per_variant;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != PKR_OK) return rc;
+    if ((rc = set_variant(P, best)) != PKR_OK) return rc;
+    // keep the invariant that the latest Phi is written
+    if ((rc = launch_one(P, kWritePhi, false)) != PKR_OK) return rc;
+    PKR_CK(cudaStreamSynchronize(P->stream));
+    if (best_variant) *best_variant = best;
+    if (best_ms_per_step) *best_ms_per_step = best_ms;
     return PKR_OK;
 }
 

@@ -45,7 +45,7 @@ __host__ __device__ constexpr int cls_begin(int c)
 }
 
 template <int I, int N, typename F>
-__device__ __forceinline__ void static_for(F&& f)
+__host__ __device__ __forceinline__ void static_for(F&& f)
 {
     if constexpr (I < N) {
         f(std::integral_constant<int, I>{});
@@ -90,11 +90,39 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <class L, typename T>
+// Launch geometry of the staged sweep.  A tile's Q velocities are split
+// among G warps (velocity groups): splitting cuts the shared memory a warp
+// stages by G and so lets an SM hold more warps, at the price of two
+// named-barrier meetings per tile.  A block carries TILES tiles.  Several
+// (G, TILES) variants are compiled per lattice and storage type; a plan picks
+// one (default table below, or pkr_plan_autotune).
+template <class L, typename T, int G_, int TILES_>
 struct Staged {
-    static constexpr int WARPS = 2;                 // warps per block
     static constexpr int Q = L::Q;
-    static constexpr size_t smem_bytes() { return (size_t)WARPS * Q * 32 * sizeof(T); }
+    static constexpr int G = G_;
+    static constexpr int TILES = TILES_;
+    static constexpr int WARPS = G * TILES;
+    static constexpr int CH = (Q + G - 1) / G;     // most velocities a warp stages
+    static constexpr size_t smem_bytes() { return (size_t)WARPS * CH * 32 * sizeof(T); }
+    static constexpr int lo(int g) { return g * Q / G; }
+};
+
+// Variant list: (G, TILES) pairs.  Small sets are never split.
+struct Geo {
+    int G, TILES;
+};
+template <class L>
+struct Variants {
+    static constexpr int N = (L::Q > 64) ? 6 : 2;
+    static constexpr Geo at(int k)
+    {
+        if (L::Q > 64) {
+            constexpr Geo big[6] = {{1, 2}, {2, 1}, {2, 2}, {3, 1}, {3, 2}, {4, 1}};
+            return big[k];
+        }
+        constexpr Geo small[2] = {{1, 2}, {1, 4}};
+        return small[k];
+    }
 };
 
 // Density of one site from its Q pulled values in shared memory (stride 32)
@@ -149,31 +177,30 @@ __device__ __forceinline__ long long fixed_term(double v, int emax)
     return b < 0 ? -t : t;
 }
 
-template <int Q>
-__device__ __forceinline__ double density_fixed(uint32_t col)   // col: shared address, stride 256 B
+// Largest exponent among N staged binary64 values (stride 256 B).
+template <int N>
+__device__ __forceinline__ int max_exponent(uint32_t col)
 {
-    constexpr int GB = 63 - 53 - ceil_log2(Q);
-    constexpr int U = 8;
-    static_assert(GB >= 1, "too many velocities for the 64-bit density sum");
-    // largest exponent: max of the high words with the sign cleared
     int h0 = 0, h1 = 0, h2 = 0, h3 = 0;
 #pragma unroll 2
-    for (int k = 0; k + 3 < Q; k += 4) {
+    for (int k = 0; k + 3 < N; k += 4) {
         h0 = max(h0, lds_hi32(col + (k + 0) * 256) & 0x7fffffff);
         h1 = max(h1, lds_hi32(col + (k + 1) * 256) & 0x7fffffff);
         h2 = max(h2, lds_hi32(col + (k + 2) * 256) & 0x7fffffff);
         h3 = max(h3, lds_hi32(col + (k + 3) * 256) & 0x7fffffff);
     }
 #pragma unroll
-    for (int k = Q - Q % 4; k < Q; ++k) h0 = max(h0, lds_hi32(col + k * 256) & 0x7fffffff);
-    const int emax = max(max(h0, h1), max(h2, h3)) >> 20;
-    if (emax == 0x7ff || emax < 64) {
-        double s = 0.0;
-        for (int k = 0; k < Q; ++k) s += lds_f64(col + k * 256);
-        return s;
-    }
+    for (int k = N - N % 4; k < N; ++k) h0 = max(h0, lds_hi32(col + k * 256) & 0x7fffffff);
+    return max(max(h0, h1), max(h2, h3)) >> 20;
+}
+
+// Fixed-point sum of N staged binary64 values aligned to emax (GB guard bits).
+template <int GB, int N>
+__device__ __forceinline__ long long fixed_sum(uint32_t col, int emax)
+{
+    constexpr int U = 8;
     long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    for (int k = 0; k + U - 1 < Q; k += U) {
+    for (int k = 0; k + U - 1 < N; k += U) {
         double v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) v[u] = lds_f64(col + (k + u) * 256);
@@ -183,9 +210,26 @@ __device__ __forceinline__ double density_fixed(uint32_t col)   // col: shared a
         a3 += fixed_term<GB>(v[3], emax) + fixed_term<GB>(v[7], emax);
     }
 #pragma unroll
-    for (int k = Q - Q % U; k < Q; ++k) a0 += fixed_term<GB>(lds_f64(col + k * 256), emax);
-    return (double)((a0 + a1) + (a2 + a3)) *
-           __longlong_as_double((long long)(emax - 52 - GB) << 52);
+    for (int k = N - N % U; k < N; ++k) a0 += fixed_term<GB>(lds_f64(col + k * 256), emax);
+    return (a0 + a1) + (a2 + a3);
+}
+
+template <int N>
+__device__ __forceinline__ double plain_sum(uint32_t col)
+{
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += lds_f64(col + k * 256);
+    return s;
+}
+
+// emax out of the range the fixed-point sum handles: Inf/NaN, or every value
+// below 2^-960 (take the plain binary64 sum then).
+__device__ __forceinline__ bool plain_path(int emax) { return emax == 0x7ff || emax < 64; }
+
+template <int GB>
+__device__ __forceinline__ double fixed_value(long long acc, int emax)
+{
+    return (double)acc * __longlong_as_double((long long)(emax - 52 - GB) << 52);
 }
 
 template <int Q>
@@ -209,31 +253,31 @@ template <typename T> __device__ __forceinline__ T lds_val(uint32_t addr);
 template <> __device__ __forceinline__ double lds_val<double>(uint32_t addr) { return lds_f64(addr); }
 template <> __device__ __forceinline__ float lds_val<float>(uint32_t addr) { return lds_f32(addr); }
 
-template <int Q, typename T> struct Density;
-template <int Q> struct Density<Q, double> {
-    static __device__ __forceinline__ double run(uint32_t col) { return density_fixed<Q>(col); }
-};
-template <int Q> struct Density<Q, float> {
-    static __device__ __forceinline__ float run(uint32_t col) { return density_fixed_f32<Q>(col); }
-};
-
-template <class L, typename T>
-__global__ void __launch_bounds__(Staged<L, T>::WARPS * 32)
+template <class L, typename T, int G_, int TILES_>
+__global__ void __launch_bounds__(G_ * TILES_ * 32)
 sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
 {
     using R = typename AccType<T>::type;
+    using ST = Staged<L, T, G_, TILES_>;
     constexpr int Q = L::Q;
-    constexpr int WARPS = Staged<L, T>::WARPS;
+    constexpr int G = ST::G;
+    constexpr int TILES = ST::TILES;
     constexpr int RC = reach_of<L>();
     constexpr int W = 2 * RC + 1;
     constexpr int NC = ncls_of<L>();
+    constexpr int GB = 63 - 53 - ceil_log2(Q);
+    static_assert(GB >= 1, "too many velocities for the 64-bit density sum");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double rpart[WARPS][3];
+    __shared__ double rpart[TILES][3];
+    __shared__ long long xacc[TILES][G][32];   // per-group partial densities of a tile
+    __shared__ int xexp[TILES][G][32];         // per-group largest exponents
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    T* col = reinterpret_cast<T*>(smem_raw) + (size_t)wib * Q * 32 + lane;
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(col);
+    const int grp = wib % G;     // velocity group of this warp
+    const int sub = wib / G;     // tile slot of this warp in the block
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(
+        reinterpret_cast<T*>(smem_raw) + (size_t)wib * ST::CH * 32 + lane);
     const T* __restrict__ A = static_cast<const T*>(a.A);
     T* __restrict__ B = static_cast<T*>(a.B);
     const T* __restrict__ S = static_cast<const T*>(a.S);
@@ -241,8 +285,8 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     const int nxy = a.nx * a.ny;
 
     double rd2 = 0.0, rn2 = 0.0, rmx = 0.0;
-    const int nw = gridDim.x * WARPS;
-    for (int tile = blockIdx.x * WARPS + wib; tile < a.ntiles; tile += nw) {
+    const int nt = gridDim.x * TILES;
+    for (int tile = blockIdx.x * TILES + sub; tile < a.ntiles; tile += nt) {
         const int64_t s64 = (int64_t)tile * 32 + lane;
         const bool valid = s64 < V;
         const int s = valid ? (int)s64 : 0;
@@ -264,74 +308,143 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
             }
         }
         const int nbytes = (valid && !a.zero_in) ? (int)sizeof(T) : 0;
-        static_for<0, Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr int ox = vx_of<L>(i) + RC;
-            constexpr int oy = vy_of<L>(i) + RC;
-            constexpr int oz = vz_of<L>(i) + RC;
-            const T* src = A + ((int64_t)i * V + (zo[oz] + yo[oy] + xs[ox]));
-            cp_async<sizeof(T)>(sbase + (uint32_t)(i * 32 * sizeof(T)), src, nbytes);
-        });
-        cp_async_wait_all();
-
-        const R Phi = Density<Q, T>::run(sbase);
         const R Sx = valid ? (R)S[s] : R(0);
-        if (valid) {
-            // relax and store, one symmetry class at a time (velocities of a
-            // class are contiguous and share phi_c, chi_c)
-            static_for<0, NC>([&](auto CI) {
-                constexpr int cl = decltype(CI)::value;
-                constexpr int i0 = cls_begin<L>(cl);
-                constexpr int i1 = cls_begin<L>(cl + 1);
-                const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
-                T* dst = B + ((int64_t)i0 * V + s);
-                int i = i0;
-                for (; i + 3 < i1; i += 4) {
-                    const R g0 = lds_val<T>(sbase + (i + 0) * 32 * sizeof(T));
-                    const R g1 = lds_val<T>(sbase + (i + 1) * 32 * sizeof(T));
-                    const R g2 = lds_val<T>(sbase + (i + 2) * 32 * sizeof(T));
-                    const R g3 = lds_val<T>(sbase + (i + 3) * 32 * sizeof(T));
-                    store_stream(dst, (T)fma(c.om1, g0, e));
-                    store_stream(dst + V, (T)fma(c.om1, g1, e));
-                    store_stream(dst + 2 * V, (T)fma(c.om1, g2, e));
-                    store_stream(dst + 3 * V, (T)fma(c.om1, g3, e));
-                    dst += 4 * V;
-                }
-                for (; i < i1; ++i) {
-                    store_stream(dst, (T)fma(c.om1, (R)lds_val<T>(sbase + i * 32 * sizeof(T)), e));
-                    dst += V;
-                }
+
+        static_for<0, G>([&](auto GI) {
+            constexpr int g = decltype(GI)::value;
+            constexpr int lo = ST::lo(g);
+            constexpr int hi = ST::lo(g + 1);
+            constexpr int n = hi - lo;
+            if (grp != g) return;
+            // pull: one asynchronous copy per velocity of this group
+            static_for<lo, hi>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int ox = vx_of<L>(i) + RC;
+                constexpr int oy = vy_of<L>(i) + RC;
+                constexpr int oz = vz_of<L>(i) + RC;
+                const T* src = A + ((int64_t)i * V + (zo[oz] + yo[oy] + xs[ox]));
+                cp_async<sizeof(T)>(sbase + (uint32_t)((i - lo) * 32 * sizeof(T)), src, nbytes);
             });
-        }
-        if (a.mode != kPlain && valid) {
-            const double ph = (double)Phi;
-            if (a.mode == kCheck) {
-                const double d = ph - a.Phi[s];
-                rd2 += d * d;
-                rn2 += ph * ph;
-                rmx = fmax(rmx, fabs(d));
+            cp_async_wait_all();
+
+            // density (the G warps of a tile meet twice at named barrier 1 + sub;
+            // both barriers sit outside every lane-dependent branch)
+            R Phi;
+            if constexpr (std::is_same<T, double>::value) {
+                int emax = max_exponent<n>(sbase);
+                if constexpr (G > 1) {
+                    xexp[sub][g][lane] = emax;
+                    asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+#pragma unroll
+                    for (int k = 0; k < G; ++k) emax = max(emax, xexp[sub][k][lane]);
+                }
+                const bool plain = plain_path(emax);
+                long long part = plain ? __double_as_longlong(plain_sum<n>(sbase))
+                                       : fixed_sum<GB, n>(sbase, emax);
+                if constexpr (G > 1) {
+                    xacc[sub][g][lane] = part;
+                    asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+                    if (plain) {
+                        double t = 0.0;
+#pragma unroll
+                        for (int k = 0; k < G; ++k) t += __longlong_as_double(xacc[sub][k][lane]);
+                        Phi = t;
+                    } else {
+                        long long t = 0;
+#pragma unroll
+                        for (int k = 0; k < G; ++k) t += xacc[sub][k][lane];
+                        Phi = fixed_value<GB>(t, emax);
+                    }
+                } else {
+                    Phi = plain ? __longlong_as_double(part) : fixed_value<GB>(part, emax);
+                }
+            } else {
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 2
+                for (int k = 0; k + 3 < n; k += 4) {
+                    s0 += lds_f32(sbase + (k + 0) * 128);
+                    s1 += lds_f32(sbase + (k + 1) * 128);
+                    s2 += lds_f32(sbase + (k + 2) * 128);
+                    s3 += lds_f32(sbase + (k + 3) * 128);
+                }
+#pragma unroll
+                for (int k = n - n % 4; k < n; ++k) s0 += lds_f32(sbase + k * 128);
+                float part = (s0 + s1) + (s2 + s3);
+                if constexpr (G > 1) {
+                    // binary32 partials meet in group order (fixed, deterministic)
+                    xacc[sub][g][lane] = (long long)__float_as_int(part);
+                    asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+                    part = 0.f;
+#pragma unroll
+                    for (int k = 0; k < G; ++k) part += __int_as_float((int)xacc[sub][k][lane]);
+                }
+                Phi = part;
             }
-            a.Phi[s] = ph;
-        }
+
+            // relax and store this group's velocities, one symmetry class at a
+            // time (velocities of a class are contiguous and share phi_c, chi_c)
+            if (valid) {
+                static_for<0, NC>([&](auto CI) {
+                    constexpr int cl = decltype(CI)::value;
+                    constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
+                    constexpr int i0 = cb > lo ? cb : lo;
+                    constexpr int i1 = ce < hi ? ce : hi;
+                    if constexpr (i0 < i1) {
+                        const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
+                        T* dst = B + ((int64_t)i0 * V + s);
+                        int i = i0;
+                        for (; i + 3 < i1; i += 4) {
+                            const R g0 = lds_val<T>(sbase + (i + 0 - lo) * 32 * sizeof(T));
+                            const R g1 = lds_val<T>(sbase + (i + 1 - lo) * 32 * sizeof(T));
+                            const R g2 = lds_val<T>(sbase + (i + 2 - lo) * 32 * sizeof(T));
+                            const R g3 = lds_val<T>(sbase + (i + 3 - lo) * 32 * sizeof(T));
+                            store_stream(dst, (T)fma(c.om1, g0, e));
+                            store_stream(dst + V, (T)fma(c.om1, g1, e));
+                            store_stream(dst + 2 * V, (T)fma(c.om1, g2, e));
+                            store_stream(dst + 3 * V, (T)fma(c.om1, g3, e));
+                            dst += 4 * V;
+                        }
+                        for (; i < i1; ++i) {
+                            const R gi = lds_val<T>(sbase + (i - lo) * 32 * sizeof(T));
+                            store_stream(dst, (T)fma(c.om1, gi, e));
+                            dst += V;
+                        }
+                    }
+                });
+            }
+            // density output and residual partials (one group per tile)
+            if (g == 0 && a.mode != kPlain && valid) {
+                const double ph = (double)Phi;
+                if (a.mode == kCheck) {
+                    const double d = ph - a.Phi[s];
+                    rd2 += d * d;
+                    rn2 += ph * ph;
+                    rmx = fmax(rmx, fabs(d));
+                }
+                a.Phi[s] = ph;
+            }
+        });
         __syncwarp();
     }
 
     if (a.mode == kCheck) {
+        if (grp == 0) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            rd2 += __shfl_down_sync(0xffffffffu, rd2, o);
-            rn2 += __shfl_down_sync(0xffffffffu, rn2, o);
-            rmx = fmax(rmx, __shfl_down_sync(0xffffffffu, rmx, o));
-        }
-        if (lane == 0) {
-            rpart[wib][0] = rd2;
-            rpart[wib][1] = rn2;
-            rpart[wib][2] = rmx;
+            for (int o = 16; o > 0; o >>= 1) {
+                rd2 += __shfl_down_sync(0xffffffffu, rd2, o);
+                rn2 += __shfl_down_sync(0xffffffffu, rn2, o);
+                rmx = fmax(rmx, __shfl_down_sync(0xffffffffu, rmx, o));
+            }
+            if (lane == 0) {
+                rpart[sub][0] = rd2;
+                rpart[sub][1] = rn2;
+                rpart[sub][2] = rmx;
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-            for (int k = 0; k < WARPS; ++k) {
+            for (int k = 0; k < TILES; ++k) {
                 t0 += rpart[k][0];
                 t1 += rpart[k][1];
                 t2 = fmax(t2, rpart[k][2]);
@@ -343,35 +456,63 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     }
 }
 
-template <class L, typename T>
-int launch_sweep_t(int variant, const SweepArgs& a, const void* coefs, int grid, void* stream)
+template <class L, typename T, int K>
+int launch_variant(const SweepArgs& a, const void* coefs, int grid, void* stream)
 {
     using R = typename AccType<T>::type;
-    const Coefs<R>& c = *static_cast<const Coefs<R>*>(coefs);
-    (void)variant;
-    constexpr int threads = Staged<L, T>::WARPS * 32;
-    const size_t smem = Staged<L, T>::smem_bytes();
-    sweep_staged_kernel<L, T><<<grid, threads, smem, (cudaStream_t)stream>>>(a, c);
+    constexpr Geo geo = Variants<L>::at(K);
+    using ST = Staged<L, T, geo.G, geo.TILES>;
+    sweep_staged_kernel<L, T, geo.G, geo.TILES><<<grid, ST::WARPS * 32, ST::smem_bytes(),
+                                                  (cudaStream_t)stream>>>(
+        a, *static_cast<const Coefs<R>*>(coefs));
     return (int)cudaGetLastError();
 }
 
-template <class L, typename T>
-int occupancy_t(int variant, int* blocks)
+template <class L, typename T, int K>
+int occupancy_variant(int* blocks, int* tiles_per_block)
 {
-    (void)variant;
-    constexpr int threads = Staged<L, T>::WARPS * 32;
-    const size_t smem = Staged<L, T>::smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(sweep_staged_kernel<L, T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr Geo geo = Variants<L>::at(K);
+    using ST = Staged<L, T, geo.G, geo.TILES>;
+    auto kern = sweep_staged_kernel<L, T, geo.G, geo.TILES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ST::smem_bytes());
     if (e != cudaSuccess) return (int)e;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sweep_staged_kernel<L, T>,
-                                                              threads, smem);
+    *tiles_per_block = geo.TILES;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, ST::WARPS * 32,
+                                                              ST::smem_bytes());
 }
+
+// Run-time dispatch over the compiled variants of (L, T).
+template <class L, typename T>
+int launch_sweep_t(int variant, const SweepArgs& a, const void* coefs, int grid, void* stream)
+{
+    int rc = (int)cudaErrorInvalidValue;
+    static_for<0, Variants<L>::N>([&](auto K) {
+        if (variant == decltype(K)::value)
+            rc = launch_variant<L, T, decltype(K)::value>(a, coefs, grid, stream);
+    });
+    return rc;
+}
+
+template <class L, typename T>
+int occupancy_t(int variant, int* blocks, int* tiles_per_block)
+{
+    int rc = (int)cudaErrorInvalidValue;
+    static_for<0, Variants<L>::N>([&](auto K) {
+        if (variant == decltype(K)::value)
+            rc = occupancy_variant<L, T, decltype(K)::value>(blocks, tiles_per_block);
+    });
+    return rc;
+}
+
+template <class L>
+int variant_count_t() { return Variants<L>::N; }
 
 #define PKR_INSTANTIATE_SWEEP(L)                                                             \
     template int launch_sweep_t<L, double>(int, const SweepArgs&, const void*, int, void*); \
     template int launch_sweep_t<L, float>(int, const SweepArgs&, const void*, int, void*);  \
-    template int occupancy_t<L, double>(int, int*);                                          \
-    template int occupancy_t<L, float>(int, int*);
+    template int occupancy_t<L, double>(int, int*, int*);                                    \
+    template int occupancy_t<L, float>(int, int*, int*);                                     \
+    template int variant_count_t<L>();
 
 }  // namespace pkr

@@ -221,3 +221,56 @@ def test_full_size_256_sampled(pk):
         window = S[np.ix_((z - off) % 256, (y - off) % 256, (x - off) % 256)]
         diffs.append(got[z, y, x] - float(np.sum(K * window)))
     assert np.max(np.abs(diffs)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("lattice,order,shape,prec", [
+    ("D3Q111", 5, (9, 7, 13), "fp64"),
+    ("D3Q111", 5, (9, 7, 13), "fp32"),
+    ("D2Q169", 7, (21, 19), "fp64"),
+    ("D2Q81", 5, (17, 23), "fp64"),
+    ("D3Q19", 1, (7, 9, 11), "fp64"),
+    ("D1Q13", 7, (100,), "fp32"),
+])
+def test_every_kernel_variant(pk, lattice, order, shape, prec):
+    """Every compiled (velocity groups x tiles) geometry gives the oracle's
+    result; in binary64 they agree bit for bit (the fixed-point density sum is
+    exact whatever the split)."""
+    rho = _rand(shape, 13)
+    steps = 11
+    n = pk._pkr.pkr_variant_count(pk.LATTICES[lattice])
+    assert n >= 2
+    ref = oracle.solve(rho, lattice, order, tau_lb=1.3, max_steps=steps).phi
+    outs = []
+    for v in range(n):
+        import torch
+        prob = pk.problem(lattice, rho.shape, order, tau_lb=1.3, max_sweeps=steps,
+                          precision=prec, variant=v)
+        r = torch.from_numpy(rho).cuda()
+        phi = torch.empty_like(r)
+        rc, st = pk.solve(r, phi, prob)
+        assert rc == 0
+        outs.append(phi.cpu().numpy())
+    for o in outs:
+        assert _rel(o, ref) <= (FP64_TOL if prec == "fp64" else 2e-5)
+    if prec == "fp64":
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+
+
+def test_autotune_advances_real_steps(pk):
+    import torch
+    rho = _rand((16, 12, 20), 14)
+    prob = pk.problem("D3Q111", rho.shape, 5, tau_lb=1.2, max_sweeps=100)
+    r = torch.from_numpy(rho).cuda()
+    out = torch.empty_like(r)
+    n = pk._pkr.pkr_variant_count(pk.LATTICES["D3Q111"])
+    with pk.Plan(prob) as P:
+        P.load_source(r)
+        best, ms = P.autotune(2)
+        assert 0 <= best < n and ms > 0
+        t = P.steps()
+        assert t == (1 + 2) * n + 1
+        P.run(3)
+        P.phi(out)
+    ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.2, max_steps=t + 3).phi
+    assert _rel(out.cpu().numpy(), ref) <= FP64_TOL
