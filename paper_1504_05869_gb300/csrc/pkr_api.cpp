@@ -58,14 +58,15 @@ int variant_count(int lattice)
     return -1;
 }
 
-// Default geometry per (lattice, storage), from autotuning runs on GB300
-// (256^3 D3Q111, 256^3 D3Q19); index into the lattice's variant list
-// {(G,TILES)} = {(1,2),(2,1),(2,2),(3,1),(3,2),(4,1)} for Q > 64, else
+// Default geometry per lattice, from timing every variant on GB300 at 256^3
+// (D3Q111: (2,2) fastest in binary64, 2.15 GLUPS, and binary32, 5.57 GLUPS;
+// D3Q19: the two variants within 0.2 %).  Index into the lattice's variant
+// list {(G,TILES)} = {(1,2),(2,1),(2,2),(3,1),(3,2),(4,1)} for Q > 64, else
 // {(1,2),(1,4)}.
 int default_variant(int lattice, int precision)
 {
-    if (variant_count(lattice) > 2) return precision == PKR_FP64 ? 3 : 0;
-    return 0;
+    (void)precision;
+    return variant_count(lattice) > 2 ? 2 : 0;
 }
 
 int elem_bytes(int precision) { return precision == PKR_FP64 ? 8 : 4; }
