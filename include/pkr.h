@@ -194,6 +194,69 @@ int pkr_solve(const pkr_problem *problem, const double *rho, double *phi, int ho
               pkr_stats *stats, void *stream);
 
 /* ---------------------------------------------------------------------
+ * Batches and serving: a context advances many independent periodic solves
+ * (same lattice, order and storage) together, one persistent kernel launch
+ * per step over all live grids, K steps per captured CUDA graph.  Requests
+ * are admitted first-fit while their device bytes fit the HBM budget, join at
+ * the next K-step boundary, and retire when their own residual check (every
+ * K steps of their own age) passes; the freed memory admits the next ones.
+ * A grid's result does not depend on what else is in the batch.
+ * --------------------------------------------------------------------- */
+typedef struct pkr_ctx pkr_ctx;
+
+typedef struct pkr_ctx_config {
+    int32_t lattice;          /* pkr_lattice of every request */
+    int32_t order;            /* expansion order N of every request */
+    int32_t precision;        /* pkr_precision of every request */
+    int32_t check_every;      /* K: steps per graph replay and per residual check (>= 1) */
+    size_t hbm_budget_bytes;  /* device bytes the live requests may hold */
+    int32_t variant;          /* >= 0: kernel geometry; -1: library default;
+                                 -2: autotune on a probe grid of edge probe_edge */
+    int32_t probe_edge;       /* edge of the cubic probe grid for variant = -2 */
+    int32_t threaded;         /* 1: a worker thread drives the batch; 0: pkr_ctx_run does */
+    int32_t max_grids;        /* most requests live at once (<= 0: 4096) */
+} pkr_ctx_config;
+
+/* Create a context on the current device.  stream: the stream all its work
+ * is queued on.  Errors: PKR_EINVAL, PKR_ENOMEM, PKR_ECUDA. */
+int pkr_ctx_create(const pkr_ctx_config *config, void *stream, pkr_ctx **out);
+
+/* Queue a request.  problem: its grid, tau/Kn, eps, tol, tol_kind and
+ * max_sweeps (lattice, order and precision must match the context).  rho: V
+ * doubles; phi: V doubles written when the request finishes (device pointers,
+ * or host pointers when host_buffers != 0); both must stay valid until then.
+ * ticket: the request's id.  Errors: PKR_EINVAL, PKR_ENOMEM (the request alone
+ * exceeds the budget). */
+int pkr_submit(pkr_ctx *ctx, const pkr_problem *problem, const double *rho, double *phi,
+               int host_buffers, uint64_t *ticket);
+
+/* State of a request: PKR_EBUSY while queued or running, otherwise its final
+ * status (PKR_OK, PKR_ENOCONV, PKR_EDIVERGED, PKR_EINVAL for a source with
+ * NaN/Inf, PKR_ECUDA); stats (may be NULL) is filled once it has finished:
+ * sweeps, residual, rho_mean_removed, tau_lb, cs2, and wall_ms = completion
+ * minus submission. */
+int pkr_poll(pkr_ctx *ctx, uint64_t ticket, pkr_stats *stats);
+
+/* Drive a non-threaded context from the caller's thread: admit what fits and
+ * run K-step windows until nothing is queued or live, or max_windows windows
+ * have run (max_windows <= 0: no limit).  Returns PKR_OK or PKR_ECUDA. */
+int pkr_ctx_run(pkr_ctx *ctx, int64_t max_windows);
+
+/* Block until a request has finished (threaded contexts) and return as
+ * pkr_poll does. */
+int pkr_ctx_wait(pkr_ctx *ctx, uint64_t ticket, pkr_stats *stats);
+
+/* Counters: requests finished, site updates performed, windows run, bytes
+ * currently held, kernel variant in use.  Any pointer may be NULL. */
+int pkr_ctx_info(pkr_ctx *ctx, int64_t *finished, double *site_updates, int64_t *windows,
+                 size_t *bytes_in_use, int32_t *variant);
+
+/* Stop the worker (if any), drop queued and running requests (their phi is
+ * not written), free everything.  The context and its tickets are invalid
+ * afterwards. */
+int pkr_ctx_destroy(pkr_ctx *ctx);
+
+/* ---------------------------------------------------------------------
  * Allocation-free residual (the paper has no counterpart: this is a service
  * for callers that cannot allocate device memory -- code that runs while a
  * CUDA graph is being captured, runtimes whose device memory all belongs to

@@ -10,8 +10,9 @@ from __future__ import annotations
 import ctypes
 
 from . import _pkr
-from ._pkr import (LATTICE_DIM, LATTICES, PKR_FP32, PKR_FP64, PKR_TOL_MAX_ABS_DPHI,  # noqa: F401
-                   PKR_TOL_REL_L2_DPHI, PkrError, check, pkr_problem, pkr_stats)
+from ._pkr import (LATTICE_DIM, LATTICES, PKR_EBUSY, PKR_FP32, PKR_FP64,  # noqa: F401
+                   PKR_TOL_MAX_ABS_DPHI, PKR_TOL_REL_L2_DPHI, PkrError, check, pkr_ctx_config,
+                   pkr_problem, pkr_stats)
 
 PRECISIONS = {"fp64": PKR_FP64, "fp32": PKR_FP32}
 TOL_KINDS = {"max_abs": PKR_TOL_MAX_ABS_DPHI, "rel_l2": PKR_TOL_REL_L2_DPHI}
@@ -137,6 +138,91 @@ class Plan:
         if self._h:
             _pkr.pkr_plan_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """Batch / serving context (pkr_ctx_*): many solves advanced together."""
+
+    def __init__(self, lattice: str, order: int, precision: str = "fp32",
+                 check_every: int = 32, hbm_budget_bytes: int = 150 * 10 ** 9,
+                 variant: int = -1, probe_edge: int = 64, threaded: bool = False,
+                 max_grids: int = 4096, stream=None):
+        cfg = pkr_ctx_config()
+        cfg.lattice = LATTICES[lattice]
+        cfg.order = int(order)
+        cfg.precision = PRECISIONS[precision]
+        cfg.check_every = int(check_every)
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.variant = int(variant)
+        cfg.probe_edge = int(probe_edge)
+        cfg.threaded = int(bool(threaded))
+        cfg.max_grids = int(max_grids)
+        self.lattice, self.order, self.precision = lattice, order, precision
+        self._h = ctypes.c_void_p()
+        self._keep = {}
+        if stream is None:
+            # a stream of its own, so that each window can be a captured graph
+            import torch
+            stream = torch.cuda.Stream()
+        self.stream = stream
+        check(_pkr.pkr_ctx_create(ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(self._h)),
+              "pkr_ctx_create")
+
+    def submit(self, rho, phi, shape=None, **kw):
+        """Queue a solve; rho/phi device tensors or host arrays (kept alive
+        here until the request finishes).  kw: problem() arguments."""
+        prob = problem(self.lattice, shape if shape is not None else rho.shape, self.order,
+                       precision=self.precision, **kw)
+        rp, rh = _ptr(rho)
+        pp, ph = _ptr(phi)
+        if rh != ph:
+            raise ValueError("rho and phi must both be on the device or both on the host")
+        t = ctypes.c_uint64()
+        check(_pkr.pkr_submit(self._h, ctypes.byref(prob), rp, pp, int(rh), ctypes.byref(t)),
+              "pkr_submit")
+        self._keep[t.value] = (rho, phi)
+        return t.value
+
+    def poll(self, ticket):
+        st = pkr_stats()
+        rc = _pkr.pkr_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(st))
+        return rc, (st.as_dict() if rc != PKR_EBUSY else None)
+
+    def wait(self, ticket):
+        st = pkr_stats()
+        rc = _pkr.pkr_ctx_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(st))
+        return rc, st.as_dict()
+
+    def run(self, max_windows=0):
+        check(_pkr.pkr_ctx_run(self._h, int(max_windows)), "pkr_ctx_run")
+
+    def info(self):
+        f, w = ctypes.c_int64(), ctypes.c_int64()
+        su = ctypes.c_double()
+        b = ctypes.c_size_t()
+        v = ctypes.c_int32()
+        check(_pkr.pkr_ctx_info(self._h, ctypes.byref(f), ctypes.byref(su), ctypes.byref(w),
+                                ctypes.byref(b), ctypes.byref(v)), "pkr_ctx_info")
+        return {"finished": f.value, "site_updates": su.value, "windows": w.value,
+                "bytes_in_use": b.value, "variant": v.value}
+
+    def close(self):
+        if self._h:
+            _pkr.pkr_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
 
     def __enter__(self):
         return self

@@ -30,7 +30,8 @@ EXPORTS = [
     "pkr_plan_bytes", "pkr_plan_create", "pkr_plan_destroy", "pkr_plan_load_source",
     "pkr_plan_run", "pkr_plan_sweeps", "pkr_plan_phi", "pkr_plan_steps",
     "pkr_plan_populations", "pkr_solve", "pkr_residual_noalloc", "pkr_variant_count",
-    "pkr_plan_autotune",
+    "pkr_plan_autotune", "pkr_ctx_create", "pkr_submit", "pkr_poll", "pkr_ctx_run",
+    "pkr_ctx_wait", "pkr_ctx_info", "pkr_ctx_destroy",
 ]
 
 
@@ -53,6 +54,14 @@ class pkr_stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pkr_ctx_config(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("variant", ctypes.c_int32),
+                ("probe_edge", ctypes.c_int32), ("threaded", ctypes.c_int32),
+                ("max_grids", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -82,6 +91,14 @@ _SIGS = {
     "pkr_residual_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _D, _P]),
     "pkr_variant_count": (ctypes.c_int, [ctypes.c_int]),
     "pkr_plan_autotune": (ctypes.c_int, [_P, ctypes.c_int, _I32, _D]),
+    "pkr_ctx_create": (ctypes.c_int, [ctypes.POINTER(pkr_ctx_config), _P, ctypes.POINTER(_P)]),
+    "pkr_submit": (ctypes.c_int, [_P, ctypes.POINTER(pkr_problem), _P, _P, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "pkr_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(pkr_stats)]),
+    "pkr_ctx_run": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "pkr_ctx_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(pkr_stats)]),
+    "pkr_ctx_info": (ctypes.c_int, [_P, _I64, _D, _I64, ctypes.POINTER(ctypes.c_size_t), _I32]),
+    "pkr_ctx_destroy": (ctypes.c_int, [_P]),
 }
 
 _lib = None
@@ -141,3 +158,10 @@ pkr_solve = _fn("pkr_solve")
 pkr_residual_noalloc = _fn("pkr_residual_noalloc")
 pkr_variant_count = _fn("pkr_variant_count")
 pkr_plan_autotune = _fn("pkr_plan_autotune")
+pkr_ctx_create = _fn("pkr_ctx_create")
+pkr_submit = _fn("pkr_submit")
+pkr_poll = _fn("pkr_poll")
+pkr_ctx_run = _fn("pkr_ctx_run")
+pkr_ctx_wait = _fn("pkr_ctx_wait")
+pkr_ctx_info = _fn("pkr_ctx_info")
+pkr_ctx_destroy = _fn("pkr_ctx_destroy")

@@ -38,6 +38,31 @@ struct Coefs {
 enum SweepMode { kPlain = 0, kWritePhi = 1, kCheck = 2 };
 enum SweepVariant { kStaged = 0 };
 
+// One grid of a batch (device-resident descriptor, see pkr_batch.cpp).
+template <typename R>
+struct BatchGrid {
+    void* pop[2];          // ping-pong populations
+    const void* S;         // source
+    double* Phi;           // density
+    int64_t V;
+    int nx, ny, nz, small;
+    int tile_begin;        // first batch-wide tile of this grid
+    int pad;
+    long long join;        // batch step at which the grid starts from zero
+    Coefs<R> c;
+};
+
+// Device-resident state read by every batch launch, so that a captured graph
+// stays valid while grids join and retire.
+struct BatchState {
+    const void* grids;     // BatchGrid<R>[ngrids], sorted by tile_begin
+    double* tile_partials; // 3 doubles per batch-wide tile (check steps)
+    double* grid_res;      // 3 doubles per grid (after the per-grid reduction)
+    long long step;        // batch step counter (launch index)
+    int ngrids;
+    int ntiles;
+};
+
 struct SweepArgs {
     const void* A;        // populations in (pulled), Q planes of V
     void* B;              // populations out
@@ -61,5 +86,12 @@ int launch_finalize_mean(const double* partials, int nblocks, int64_t V, double*
 int launch_make_source(const double* rho, const double* mean, double scale, int64_t V,
                        void* S, int precision, void* stream);
 int launch_finalize_residual(const double* partials, int nblocks, double* out3, void* stream);
+
+// Batch engine kernels (sweep_*.cu / pkr_kernels.cu).
+int launch_batch_step(int lattice, int precision, int variant, BatchState* state, int check_every,
+                      int grid, void* stream);
+int batch_occupancy(int lattice, int precision, int variant, int* blocks_per_sm);
+int launch_batch_reduce(BatchState* state, int max_grids, int grid_stride_bytes, void* stream);
+int launch_batch_increment(BatchState* state, void* stream);
 
 }  // namespace pkr

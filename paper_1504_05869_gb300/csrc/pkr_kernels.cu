@@ -7,6 +7,8 @@
 // repeated runs give bit-identical S.
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 #include "pkr_internal.h"
 
 namespace pkr {
@@ -116,7 +118,70 @@ finalize_residual_kernel(const double* __restrict__ partials, int n, double* out
     }
 }
 
+// Per-grid residual of a batch check step: sums the grid's tile partials in
+// tile order (deterministic), one block per grid.
+__global__ void __launch_bounds__(kRedThreads)
+batch_reduce_kernel(const BatchState* st, int stride_bytes)
+{
+    const int g = blockIdx.x;
+    if (g >= st->ngrids) return;
+    const unsigned char* base = static_cast<const unsigned char*>(st->grids);
+    const size_t off = offsetof(BatchGrid<double>, tile_begin);
+    const int tb = *reinterpret_cast<const int*>(base + (size_t)g * stride_bytes + off);
+    const int te = (g + 1 < st->ngrids)
+                       ? *reinterpret_cast<const int*>(base + (size_t)(g + 1) * stride_bytes + off)
+                       : st->ntiles;
+    const double* p = st->tile_partials;
+    __shared__ double s0[kRedThreads / 32], s1[kRedThreads / 32], s2[kRedThreads / 32];
+    double d2 = 0.0, n2 = 0.0, mx = 0.0;
+    for (int t = tb + (int)threadIdx.x; t < te; t += kRedThreads) {
+        d2 += p[3 * (int64_t)t + 0];
+        n2 += p[3 * (int64_t)t + 1];
+        mx = fmax(mx, p[3 * (int64_t)t + 2]);
+    }
+    d2 = warp_sum(d2);
+    n2 = warp_sum(n2);
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) {
+        s0[threadIdx.x >> 5] = d2;
+        s1[threadIdx.x >> 5] = n2;
+        s2[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int k = 0; k < kRedThreads / 32; ++k) {
+            a += s0[k];
+            b += s1[k];
+            c = fmax(c, s2[k]);
+        }
+        double* out = st->grid_res + 3 * g;
+        out[0] = c;
+        out[1] = (b > 0.0) ? sqrt(a) / sqrt(b) : (a == 0.0 ? 0.0 : INFINITY);
+        out[2] = sqrt(b);
+        if (!(a == a) || !(b == b)) {
+            out[0] = NAN;
+            out[1] = NAN;
+        }
+    }
+}
+
+__global__ void batch_step_increment_kernel(BatchState* st) { st->step += 1; }
+
 }  // namespace
+
+int launch_batch_reduce(BatchState* state, int max_grids, int grid_stride_bytes, void* stream)
+{
+    batch_reduce_kernel<<<max_grids, kRedThreads, 0, (cudaStream_t)stream>>>(state,
+                                                                             grid_stride_bytes);
+    return (int)cudaGetLastError();
+}
+
+int launch_batch_increment(BatchState* state, void* stream)
+{
+    batch_step_increment_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(state);
+    return (int)cudaGetLastError();
+}
 
 int launch_rho_partials(const double* rho, int64_t V, double* partials, int nblocks,
                         int* nonfinite, void* stream)

@@ -253,20 +253,189 @@ template <typename T> __device__ __forceinline__ T lds_val(uint32_t addr);
 template <> __device__ __forceinline__ double lds_val<double>(uint32_t addr) { return lds_f64(addr); }
 template <> __device__ __forceinline__ float lds_val<float>(uint32_t addr) { return lds_f32(addr); }
 
+// One grid as a tile step sees it.
+template <typename T>
+struct TileGrid {
+    const T* A;     // populations in (pulled)
+    T* B;           // populations out
+    const T* S;     // source
+    double* Phi;    // density (written on write/check sweeps)
+    int64_t V;
+    int nx, ny, nz, small;
+};
+
+// One 32-site tile of one grid, executed by the G warps of a tile slot:
+// pull (cp.async), density, relax + store, density output.  On check sweeps
+// the lane's contributions to |dPhi|^2, |Phi|^2 and max |dPhi| are added to
+// d2, n2, mx (velocity group 0 only).
+template <class L, typename T, int G, int TILES>
+__device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
+                                          const Coefs<typename AccType<T>::type>& c, int tile,
+                                          int mode, bool zero_in, int lane, int grp, int sub,
+                                          uint32_t sbase, long long (&xacc)[TILES][G][32],
+                                          int (&xexp)[TILES][G][32], double& d2, double& n2,
+                                          double& mx)
+{
+    using R = typename AccType<T>::type;
+    using ST = Staged<L, T, G, TILES>;
+    constexpr int RC = reach_of<L>();
+    constexpr int W = 2 * RC + 1;
+    constexpr int NC = ncls_of<L>();
+    constexpr int GB = 63 - 53 - ceil_log2(L::Q);
+    static_assert(GB >= 1, "too many velocities for the 64-bit density sum");
+    const T* __restrict__ A = tg.A;
+    T* __restrict__ B = tg.B;
+    const int64_t V = tg.V;
+    const int nx = tg.nx, ny = tg.ny, nz = tg.nz;
+    const int nxy = nx * ny;
+
+    const int64_t s64 = (int64_t)tile * 32 + lane;
+    const bool valid = s64 < V;
+    const int s = valid ? (int)s64 : 0;
+    const int x = s % nx;
+    const int r = s / nx;
+    const int y = r % ny;
+    const int z = r / ny;
+    int xs[W], yo[W], zo[W];
+#pragma unroll
+    for (int d = -RC; d <= RC; ++d) {
+        if (tg.small) {
+            xs[d + RC] = wrap_any(x - d, nx);
+            yo[d + RC] = wrap_any(y - d, ny) * nx;
+            zo[d + RC] = wrap_any(z - d, nz) * nxy;
+        } else {
+            xs[d + RC] = wrap_near(x - d, nx);
+            yo[d + RC] = wrap_near(y - d, ny) * nx;
+            zo[d + RC] = wrap_near(z - d, nz) * nxy;
+        }
+    }
+    const int nbytes = (valid && !zero_in) ? (int)sizeof(T) : 0;
+    const R Sx = valid ? (R)tg.S[s] : R(0);
+
+    static_for<0, G>([&](auto GI) {
+        constexpr int g = decltype(GI)::value;
+        constexpr int lo = ST::lo(g);
+        constexpr int hi = ST::lo(g + 1);
+        constexpr int n = hi - lo;
+        if (grp != g) return;
+        // pull: one asynchronous copy per velocity of this group
+        static_for<lo, hi>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int ox = vx_of<L>(i) + RC;
+            constexpr int oy = vy_of<L>(i) + RC;
+            constexpr int oz = vz_of<L>(i) + RC;
+            const T* src = A + ((int64_t)i * V + (zo[oz] + yo[oy] + xs[ox]));
+            cp_async<sizeof(T)>(sbase + (uint32_t)((i - lo) * 32 * sizeof(T)), src, nbytes);
+        });
+        cp_async_wait_all();
+
+        // density (the G warps of a tile meet twice at named barrier 1 + sub;
+        // both barriers sit outside every lane-dependent branch)
+        R Phi;
+        if constexpr (std::is_same<T, double>::value) {
+            int emax = max_exponent<n>(sbase);
+            if constexpr (G > 1) {
+                xexp[sub][g][lane] = emax;
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+#pragma unroll
+                for (int k = 0; k < G; ++k) emax = max(emax, xexp[sub][k][lane]);
+            }
+            const bool plain = plain_path(emax);
+            long long part = plain ? __double_as_longlong(plain_sum<n>(sbase))
+                                   : fixed_sum<GB, n>(sbase, emax);
+            if constexpr (G > 1) {
+                xacc[sub][g][lane] = part;
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+                if (plain) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int k = 0; k < G; ++k) t += __longlong_as_double(xacc[sub][k][lane]);
+                    Phi = t;
+                } else {
+                    long long t = 0;
+#pragma unroll
+                    for (int k = 0; k < G; ++k) t += xacc[sub][k][lane];
+                    Phi = fixed_value<GB>(t, emax);
+                }
+            } else {
+                Phi = plain ? __longlong_as_double(part) : fixed_value<GB>(part, emax);
+            }
+        } else {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 2
+            for (int k = 0; k + 3 < n; k += 4) {
+                s0 += lds_f32(sbase + (k + 0) * 128);
+                s1 += lds_f32(sbase + (k + 1) * 128);
+                s2 += lds_f32(sbase + (k + 2) * 128);
+                s3 += lds_f32(sbase + (k + 3) * 128);
+            }
+#pragma unroll
+            for (int k = n - n % 4; k < n; ++k) s0 += lds_f32(sbase + k * 128);
+            float part = (s0 + s1) + (s2 + s3);
+            if constexpr (G > 1) {
+                // binary32 partials meet in group order (fixed, deterministic)
+                xacc[sub][g][lane] = (long long)__float_as_int(part);
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+                part = 0.f;
+#pragma unroll
+                for (int k = 0; k < G; ++k) part += __int_as_float((int)xacc[sub][k][lane]);
+            }
+            Phi = part;
+        }
+
+        // relax and store this group's velocities, one symmetry class at a
+        // time (velocities of a class are contiguous and share phi_c, chi_c)
+        if (valid) {
+            static_for<0, NC>([&](auto CI) {
+                constexpr int cl = decltype(CI)::value;
+                constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
+                constexpr int i0 = cb > lo ? cb : lo;
+                constexpr int i1 = ce < hi ? ce : hi;
+                if constexpr (i0 < i1) {
+                    const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
+                    T* dst = B + ((int64_t)i0 * V + s);
+                    int i = i0;
+                    for (; i + 3 < i1; i += 4) {
+                        const R g0 = lds_val<T>(sbase + (i + 0 - lo) * 32 * sizeof(T));
+                        const R g1 = lds_val<T>(sbase + (i + 1 - lo) * 32 * sizeof(T));
+                        const R g2 = lds_val<T>(sbase + (i + 2 - lo) * 32 * sizeof(T));
+                        const R g3 = lds_val<T>(sbase + (i + 3 - lo) * 32 * sizeof(T));
+                        store_stream(dst, (T)fma(c.om1, g0, e));
+                        store_stream(dst + V, (T)fma(c.om1, g1, e));
+                        store_stream(dst + 2 * V, (T)fma(c.om1, g2, e));
+                        store_stream(dst + 3 * V, (T)fma(c.om1, g3, e));
+                        dst += 4 * V;
+                    }
+                    for (; i < i1; ++i) {
+                        const R gi = lds_val<T>(sbase + (i - lo) * 32 * sizeof(T));
+                        store_stream(dst, (T)fma(c.om1, gi, e));
+                        dst += V;
+                    }
+                }
+            });
+        }
+        // density output and residual contributions (one group per tile)
+        if (g == 0 && mode != kPlain && valid) {
+            const double ph = (double)Phi;
+            if (mode == kCheck) {
+                const double d = ph - tg.Phi[s];
+                d2 += d * d;
+                n2 += ph * ph;
+                mx = fmax(mx, fabs(d));
+            }
+            tg.Phi[s] = ph;
+        }
+    });
+    __syncwarp();
+}
+
 template <class L, typename T, int G_, int TILES_>
 __global__ void __launch_bounds__(G_ * TILES_ * 32)
 sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
 {
-    using R = typename AccType<T>::type;
-    using ST = Staged<L, T, G_, TILES_>;
-    constexpr int Q = L::Q;
-    constexpr int G = ST::G;
-    constexpr int TILES = ST::TILES;
-    constexpr int RC = reach_of<L>();
-    constexpr int W = 2 * RC + 1;
-    constexpr int NC = ncls_of<L>();
-    constexpr int GB = 63 - 53 - ceil_log2(Q);
-    static_assert(GB >= 1, "too many velocities for the 64-bit density sum");
+    constexpr int G = G_;
+    constexpr int TILES = TILES_;
+    using ST = Staged<L, T, G, TILES>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double rpart[TILES][3];
     __shared__ long long xacc[TILES][G][32];   // per-group partial densities of a tile
@@ -278,154 +447,14 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     const int sub = wib / G;     // tile slot of this warp in the block
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(
         reinterpret_cast<T*>(smem_raw) + (size_t)wib * ST::CH * 32 + lane);
-    const T* __restrict__ A = static_cast<const T*>(a.A);
-    T* __restrict__ B = static_cast<T*>(a.B);
-    const T* __restrict__ S = static_cast<const T*>(a.S);
-    const int64_t V = a.V;
-    const int nxy = a.nx * a.ny;
+    const TileGrid<T> tg{static_cast<const T*>(a.A), static_cast<T*>(a.B),
+                         static_cast<const T*>(a.S), a.Phi, a.V, a.nx, a.ny, a.nz, a.small};
 
     double rd2 = 0.0, rn2 = 0.0, rmx = 0.0;
     const int nt = gridDim.x * TILES;
-    for (int tile = blockIdx.x * TILES + sub; tile < a.ntiles; tile += nt) {
-        const int64_t s64 = (int64_t)tile * 32 + lane;
-        const bool valid = s64 < V;
-        const int s = valid ? (int)s64 : 0;
-        const int x = s % a.nx;
-        const int r = s / a.nx;
-        const int y = r % a.ny;
-        const int z = r / a.ny;
-        int xs[W], yo[W], zo[W];
-#pragma unroll
-        for (int d = -RC; d <= RC; ++d) {
-            if (a.small) {
-                xs[d + RC] = wrap_any(x - d, a.nx);
-                yo[d + RC] = wrap_any(y - d, a.ny) * a.nx;
-                zo[d + RC] = wrap_any(z - d, a.nz) * nxy;
-            } else {
-                xs[d + RC] = wrap_near(x - d, a.nx);
-                yo[d + RC] = wrap_near(y - d, a.ny) * a.nx;
-                zo[d + RC] = wrap_near(z - d, a.nz) * nxy;
-            }
-        }
-        const int nbytes = (valid && !a.zero_in) ? (int)sizeof(T) : 0;
-        const R Sx = valid ? (R)S[s] : R(0);
-
-        static_for<0, G>([&](auto GI) {
-            constexpr int g = decltype(GI)::value;
-            constexpr int lo = ST::lo(g);
-            constexpr int hi = ST::lo(g + 1);
-            constexpr int n = hi - lo;
-            if (grp != g) return;
-            // pull: one asynchronous copy per velocity of this group
-            static_for<lo, hi>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                constexpr int ox = vx_of<L>(i) + RC;
-                constexpr int oy = vy_of<L>(i) + RC;
-                constexpr int oz = vz_of<L>(i) + RC;
-                const T* src = A + ((int64_t)i * V + (zo[oz] + yo[oy] + xs[ox]));
-                cp_async<sizeof(T)>(sbase + (uint32_t)((i - lo) * 32 * sizeof(T)), src, nbytes);
-            });
-            cp_async_wait_all();
-
-            // density (the G warps of a tile meet twice at named barrier 1 + sub;
-            // both barriers sit outside every lane-dependent branch)
-            R Phi;
-            if constexpr (std::is_same<T, double>::value) {
-                int emax = max_exponent<n>(sbase);
-                if constexpr (G > 1) {
-                    xexp[sub][g][lane] = emax;
-                    asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
-#pragma unroll
-                    for (int k = 0; k < G; ++k) emax = max(emax, xexp[sub][k][lane]);
-                }
-                const bool plain = plain_path(emax);
-                long long part = plain ? __double_as_longlong(plain_sum<n>(sbase))
-                                       : fixed_sum<GB, n>(sbase, emax);
-                if constexpr (G > 1) {
-                    xacc[sub][g][lane] = part;
-                    asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
-                    if (plain) {
-                        double t = 0.0;
-#pragma unroll
-                        for (int k = 0; k < G; ++k) t += __longlong_as_double(xacc[sub][k][lane]);
-                        Phi = t;
-                    } else {
-                        long long t = 0;
-#pragma unroll
-                        for (int k = 0; k < G; ++k) t += xacc[sub][k][lane];
-                        Phi = fixed_value<GB>(t, emax);
-                    }
-                } else {
-                    Phi = plain ? __longlong_as_double(part) : fixed_value<GB>(part, emax);
-                }
-            } else {
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll 2
-                for (int k = 0; k + 3 < n; k += 4) {
-                    s0 += lds_f32(sbase + (k + 0) * 128);
-                    s1 += lds_f32(sbase + (k + 1) * 128);
-                    s2 += lds_f32(sbase + (k + 2) * 128);
-                    s3 += lds_f32(sbase + (k + 3) * 128);
-                }
-#pragma unroll
-                for (int k = n - n % 4; k < n; ++k) s0 += lds_f32(sbase + k * 128);
-                float part = (s0 + s1) + (s2 + s3);
-                if constexpr (G > 1) {
-                    // binary32 partials meet in group order (fixed, deterministic)
-                    xacc[sub][g][lane] = (long long)__float_as_int(part);
-                    asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
-                    part = 0.f;
-#pragma unroll
-                    for (int k = 0; k < G; ++k) part += __int_as_float((int)xacc[sub][k][lane]);
-                }
-                Phi = part;
-            }
-
-            // relax and store this group's velocities, one symmetry class at a
-            // time (velocities of a class are contiguous and share phi_c, chi_c)
-            if (valid) {
-                static_for<0, NC>([&](auto CI) {
-                    constexpr int cl = decltype(CI)::value;
-                    constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
-                    constexpr int i0 = cb > lo ? cb : lo;
-                    constexpr int i1 = ce < hi ? ce : hi;
-                    if constexpr (i0 < i1) {
-                        const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
-                        T* dst = B + ((int64_t)i0 * V + s);
-                        int i = i0;
-                        for (; i + 3 < i1; i += 4) {
-                            const R g0 = lds_val<T>(sbase + (i + 0 - lo) * 32 * sizeof(T));
-                            const R g1 = lds_val<T>(sbase + (i + 1 - lo) * 32 * sizeof(T));
-                            const R g2 = lds_val<T>(sbase + (i + 2 - lo) * 32 * sizeof(T));
-                            const R g3 = lds_val<T>(sbase + (i + 3 - lo) * 32 * sizeof(T));
-                            store_stream(dst, (T)fma(c.om1, g0, e));
-                            store_stream(dst + V, (T)fma(c.om1, g1, e));
-                            store_stream(dst + 2 * V, (T)fma(c.om1, g2, e));
-                            store_stream(dst + 3 * V, (T)fma(c.om1, g3, e));
-                            dst += 4 * V;
-                        }
-                        for (; i < i1; ++i) {
-                            const R gi = lds_val<T>(sbase + (i - lo) * 32 * sizeof(T));
-                            store_stream(dst, (T)fma(c.om1, gi, e));
-                            dst += V;
-                        }
-                    }
-                });
-            }
-            // density output and residual partials (one group per tile)
-            if (g == 0 && a.mode != kPlain && valid) {
-                const double ph = (double)Phi;
-                if (a.mode == kCheck) {
-                    const double d = ph - a.Phi[s];
-                    rd2 += d * d;
-                    rn2 += ph * ph;
-                    rmx = fmax(rmx, fabs(d));
-                }
-                a.Phi[s] = ph;
-            }
-        });
-        __syncwarp();
-    }
+    for (int tile = blockIdx.x * TILES + sub; tile < a.ntiles; tile += nt)
+        tile_step<L, T, G, TILES>(tg, c, tile, a.mode, a.zero_in != 0, lane, grp, sub, sbase,
+                                  xacc, xexp, rd2, rn2, rmx);
 
     if (a.mode == kCheck) {
         if (grp == 0) {
@@ -454,6 +483,122 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
             a.partials[3 * blockIdx.x + 2] = t2;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Batch sweep: one persistent launch advances every live grid of a batch by
+// one step.  Batch-wide tile t belongs to the grid whose tile_begin is the
+// largest one <= t (binary search over the descriptors).  A grid's age (steps
+// since it joined) picks its buffers and its own residual schedule: it writes
+// Phi when (age + 2) % K == 0 and checks when (age + 1) % K == 0 (age >= 1),
+// so a grid's trajectory and stopping step do not depend on what else is in
+// the batch.  On check steps each tile leaves its three partial sums in
+// tile_partials; pkr_batch_reduce sums them per grid in a fixed order.
+// ---------------------------------------------------------------------------
+template <class L, typename T, int G_, int TILES_>
+__global__ void __launch_bounds__(G_ * TILES_ * 32)
+sweep_batch_kernel(BatchState* st, int K)
+{
+    using R = typename AccType<T>::type;
+    constexpr int G = G_;
+    constexpr int TILES = TILES_;
+    using ST = Staged<L, T, G, TILES>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long xacc[TILES][G][32];
+    __shared__ int xexp[TILES][G][32];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int grp = wib % G;
+    const int sub = wib / G;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(
+        reinterpret_cast<T*>(smem_raw) + (size_t)wib * ST::CH * 32 + lane);
+    const BatchGrid<R>* grids = static_cast<const BatchGrid<R>*>(st->grids);
+    const int ngrids = st->ngrids;
+    const int ntiles = st->ntiles;
+    const long long step = st->step;
+    double* tpart = st->tile_partials;
+
+    const int nt = gridDim.x * TILES;
+    for (int tile = blockIdx.x * TILES + sub; tile < ntiles; tile += nt) {
+        int lo = 0, hi = ngrids - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (grids[mid].tile_begin <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchGrid<R>& gd = grids[lo];
+        const long long age = step - gd.join;
+        const int cur = (int)(age & 1);
+        const bool zero_in = (age == 0);
+        int mode = kPlain;
+        if (age >= 1 && (age + 1) % K == 0) mode = kCheck;
+        else if (zero_in || (age + 2) % K == 0) mode = kWritePhi;
+        const TileGrid<T> tg{static_cast<const T*>(gd.pop[cur]), static_cast<T*>(gd.pop[cur ^ 1]),
+                             static_cast<const T*>(gd.S), gd.Phi, gd.V, gd.nx, gd.ny, gd.nz,
+                             gd.small};
+        double d2 = 0.0, n2 = 0.0, mx = 0.0;
+        tile_step<L, T, G, TILES>(tg, gd.c, tile - gd.tile_begin, mode, zero_in, lane, grp, sub,
+                                  sbase, xacc, xexp, d2, n2, mx);
+        if (mode == kCheck && grp == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                d2 += __shfl_down_sync(0xffffffffu, d2, o);
+                n2 += __shfl_down_sync(0xffffffffu, n2, o);
+                mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            }
+            if (lane == 0) {
+                tpart[3 * (int64_t)tile + 0] = d2;
+                tpart[3 * (int64_t)tile + 1] = n2;
+                tpart[3 * (int64_t)tile + 2] = mx;
+            }
+        }
+    }
+}
+
+template <class L, typename T, int K>
+int launch_batch_variant(BatchState* st, int check_every, int grid, void* stream)
+{
+    constexpr Geo geo = Variants<L>::at(K);
+    using ST = Staged<L, T, geo.G, geo.TILES>;
+    sweep_batch_kernel<L, T, geo.G, geo.TILES><<<grid, ST::WARPS * 32, ST::smem_bytes(),
+                                                 (cudaStream_t)stream>>>(st, check_every);
+    return (int)cudaGetLastError();
+}
+
+template <class L, typename T, int K>
+int batch_occupancy_variant(int* blocks)
+{
+    constexpr Geo geo = Variants<L>::at(K);
+    using ST = Staged<L, T, geo.G, geo.TILES>;
+    auto kern = sweep_batch_kernel<L, T, geo.G, geo.TILES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ST::smem_bytes());
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, ST::WARPS * 32,
+                                                              ST::smem_bytes());
+}
+
+template <class L, typename T>
+int launch_batch_t(int variant, BatchState* st, int check_every, int grid, void* stream)
+{
+    int rc = (int)cudaErrorInvalidValue;
+    static_for<0, Variants<L>::N>([&](auto K) {
+        if (variant == decltype(K)::value)
+            rc = launch_batch_variant<L, T, decltype(K)::value>(st, check_every, grid, stream);
+    });
+    return rc;
+}
+
+template <class L, typename T>
+int batch_occupancy_t(int variant, int* blocks)
+{
+    int rc = (int)cudaErrorInvalidValue;
+    static_for<0, Variants<L>::N>([&](auto K) {
+        if (variant == decltype(K)::value)
+            rc = batch_occupancy_variant<L, T, decltype(K)::value>(blocks);
+    });
+    return rc;
 }
 
 template <class L, typename T, int K>
@@ -513,6 +658,10 @@ int variant_count_t() { return Variants<L>::N; }
     template int launch_sweep_t<L, float>(int, const SweepArgs&, const void*, int, void*);  \
     template int occupancy_t<L, double>(int, int*, int*);                                    \
     template int occupancy_t<L, float>(int, int*, int*);                                     \
-    template int variant_count_t<L>();
+    template int variant_count_t<L>();                                                      \
+    template int launch_batch_t<L, double>(int, BatchState*, int, int, void*);               \
+    template int launch_batch_t<L, float>(int, BatchState*, int, int, void*);                \
+    template int batch_occupancy_t<L, double>(int, int*);                                    \
+    template int batch_occupancy_t<L, float>(int, int*);
 
 }  // namespace pkr

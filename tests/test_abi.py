@@ -130,3 +130,23 @@ def test_plan_bytes(pkr):
     b32 = ctypes.c_size_t()
     assert pkr._pkr.pkr_plan_bytes(ctypes.byref(p32), ctypes.byref(b32)) == 0
     assert b32.value < 0.55 * b.value
+
+
+def test_context_config_validation(pk_cfg=None):
+    import paper_1504_05869_gb300 as pk
+    pk._pkr.load()
+
+    def create(**kw):
+        cfg = pk.pkr_ctx_config()
+        cfg.lattice, cfg.order, cfg.precision = pk.LATTICES["D3Q111"], 5, 1
+        cfg.check_every, cfg.hbm_budget_bytes, cfg.variant = 8, 10 ** 9, -1
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        h = ctypes.c_void_p()
+        return pk._pkr.pkr_ctx_create(ctypes.byref(cfg), None, ctypes.byref(h))
+
+    assert create(check_every=0) == -1
+    assert create(hbm_budget_bytes=0) == -1
+    assert create(precision=7) == -1
+    assert create(order=7) == -1
+    assert create(lattice=42) == -1

@@ -1,0 +1,130 @@
+"""GPU tests of the batch / serving engine (pkr_ctx_*), through the C ABI.
+
+* Every request's Phi equals the oracle's after the number of steps the
+  engine reports (binary64: <= 1e-12 relative L2; binary32 storage: <= 2e-5,
+  the binary32 rounding of each population accumulated over the run and
+  bounded by the contraction).
+* A request gives the same result alone and in a mix of other requests (bit
+  for bit: the batch kernel is deterministic per grid and each grid checks on
+  its own age).
+* Admission by HBM budget, threaded serving with host buffers, error paths.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_05869_gb300.workloads import stiff_source
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+    return pk
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+JOBS = [((12, 10, 14), 1.3, 1e-9, 4), ((9, 7, 13), 2.0, 1e-8, 5), ((16, 16, 16), 1.1, 1e-7, 6),
+        ((2, 3, 5), 1.4, 1e-9, 7), ((20, 11, 8), 3.0, 1e-6, 8)]
+
+
+def _run_ctx(pk, jobs, precision, K=8, budget=2 * 10 ** 9, threaded=False, host=False,
+             variant=-1):
+    import torch
+    ctx = pk.Context("D3Q111", 5, precision=precision, check_every=K, hbm_budget_bytes=budget,
+                     threaded=threaded, variant=variant)
+    out = []
+    for shape, tau, tol, seed in jobs:
+        rho, _ = stiff_source(shape, count=3, sigma=1.5, seed=seed)
+        if host:
+            r, phi = np.ascontiguousarray(rho), np.zeros(shape)
+        else:
+            r = torch.from_numpy(rho).cuda()
+            phi = torch.zeros_like(r)
+        t = ctx.submit(r, phi, tau_lb=tau, tol=tol, tol_kind="rel_l2", max_sweeps=20000)
+        out.append((rho, phi, t, tau, tol))
+    if not threaded:
+        ctx.run()
+    res = []
+    for rho, phi, t, tau, tol in out:
+        rc, st = ctx.wait(t) if threaded else ctx.poll(t)
+        got = phi if host else phi.cpu().numpy()
+        res.append((rho, got, rc, st, tau, tol))
+    info = ctx.info()
+    ctx.close()
+    return res, info
+
+
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_batch_matches_oracle(pk, precision, bar):
+    res, info = _run_ctx(pk, JOBS, precision)
+    assert info["finished"] == len(JOBS) and info["bytes_in_use"] == 0
+    for rho, got, rc, st, tau, tol in res:
+        assert rc == 0, rc
+        assert st["residual"] < tol
+        assert (st["sweeps"] + 1) % 8 == 0
+        ref = oracle.solve(rho, "D3Q111", 5, tau_lb=tau, max_steps=st["sweeps"]).phi
+        assert _rel(got, ref) <= bar, (rho.shape, _rel(got, ref))
+        assert abs(st["rho_mean_removed"] - rho.mean()) < 1e-15
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_same_result_alone_and_in_mix(pk, precision):
+    alone, _ = _run_ctx(pk, JOBS[:1], precision)
+    mixed, _ = _run_ctx(pk, JOBS[1:3] + JOBS[:1] + JOBS[3:], precision)
+    a = alone[0]
+    b = mixed[2]
+    assert a[3]["sweeps"] == b[3]["sweeps"]
+    assert np.array_equal(a[1], b[1])
+
+
+def test_budget_admits_one_at_a_time(pk):
+    """A budget that holds one request at a time: every request still runs,
+    one after the other, and gives the same result as with room for all."""
+    shape = (16, 16, 16)
+    one = 2 * 111 * 16 ** 3 * 4 + 16 ** 3 * 12
+    jobs = [(shape, 1.3, 1e-7, s) for s in (11, 12, 13)]
+    tight, info = _run_ctx(pk, jobs, "fp32", budget=int(1.5 * one))
+    roomy, _ = _run_ctx(pk, jobs, "fp32", budget=10 ** 9)
+    for a, b in zip(tight, roomy):
+        assert a[2] == 0 and np.array_equal(a[1], b[1])
+    assert info["windows"] >= 3 * (tight[0][3]["sweeps"] + 1) // 8
+
+
+def test_threaded_serving_host_buffers(pk):
+    res, info = _run_ctx(pk, JOBS[:3], "fp32", threaded=True, host=True)
+    for rho, got, rc, st, tau, tol in res:
+        assert rc == 0
+        ref = oracle.solve(rho, "D3Q111", 5, tau_lb=tau, max_steps=st["sweeps"]).phi
+        assert _rel(got, ref) <= 2e-5
+        assert st["wall_ms"] > 0
+
+
+def test_autotuned_context_and_errors(pk):
+    import torch
+    ctx = pk.Context("D3Q111", 5, precision="fp32", check_every=4, variant=-2, probe_edge=24,
+                     hbm_budget_bytes=10 ** 9)
+    assert 0 <= ctx.info()["variant"] < pk._pkr.pkr_variant_count(pk.LATTICES["D3Q111"])
+    big = torch.zeros((128, 128, 128), dtype=torch.float64, device="cuda")
+    with pytest.raises(pk.PkrError) as e:     # alone exceeds the budget
+        ctx.submit(big, big.clone(), tau_lb=1.3, tol=1e-6)
+    assert e.value.status == -2
+    rho, _ = stiff_source((8, 8, 8), count=2, sigma=1.5, seed=3)
+    rho[1, 2, 3] = np.nan
+    r = torch.from_numpy(rho).cuda()
+    t = ctx.submit(r, torch.zeros_like(r), tau_lb=1.3, tol=1e-6)
+    ctx.run()
+    rc, _ = ctx.poll(t)
+    assert rc == -1
+    with pytest.raises(pk.PkrError):          # unstable relaxation time
+        ctx.submit(r, torch.zeros_like(r), tau_lb=0.6, tol=1e-6)
+    ctx.close()
