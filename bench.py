@@ -313,6 +313,153 @@ def run(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (one JSON line each; the default run is the sweep above)
+# ---------------------------------------------------------------------------
+def _pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def run_batch(args):
+    """256 independent periodic 3D grids, edges log-uniform in [32, 128]
+    (seed 2), 1-16 Gaussians (sigma 1-4), D3Q111 N=5, Kn 0.2 per grid, all
+    advanced by the batch engine (one persistent launch per step, K-step
+    graphs, geometry from the autotuner) until each retires."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+    from paper_1504_05869_gb300.workloads import batch_jobs
+    jobs = batch_jobs(args.batch_count, seed=2)
+    tol = args.tol if args.tol > 0 else (1e-8 if args.precision == "fp64" else 1e-7)
+    rhos = [torch.from_numpy(j.rho()).cuda() for j in jobs]
+    phis = [torch.zeros_like(r) for r in rhos]
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    ctx = pk.Context("D3Q111", 5, precision=args.precision, check_every=SWEEPS_PER_STEP,
+                     hbm_budget_bytes=int(args.budget_gb * 1e9), variant=-2, probe_edge=64,
+                     stream=stream)
+    t0 = time.perf_counter()
+    tickets = [ctx.submit(r, p, knudsen=KN, tol=tol, tol_kind="rel_l2", max_sweeps=50000)
+               for r, p in zip(rhos, phis)]
+    ctx.run()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    info = ctx.info()
+    stats = [ctx.poll(t) for t in tickets]
+    ctx.close()
+    ok = sum(1 for rc, _ in stats if rc == 0)
+    sweeps = [st["sweeps"] for rc, st in stats if st]
+    sites = sum(r.numel() for r in rhos)
+    line = {"metric": "batched solves: GLUPS over all grids and solves/s", "workload": "batch",
+            "value": info["site_updates"] / dt / 1e9, "unit": "GLUPS",
+            "solves_per_s": ok / dt, "solves": len(jobs), "converged": ok, "seconds": dt,
+            "sites_total": sites, "site_updates": info["site_updates"],
+            "sweeps_min_median_max": [min(sweeps), _pct(sweeps, 50), max(sweeps)],
+            "precision": args.precision, "tol_rel_l2": tol, "kernel_variant": info["variant"],
+            "windows": info["windows"], "check_every": SWEEPS_PER_STEP,
+            "hbm_budget_gb": args.budget_gb, "data": "synthetic",
+            "config": {"grids": len(jobs), "edges": "log-uniform [32,128], seed 2",
+                       "lattice": "D3Q111", "order": 5, "knudsen": KN}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals (seed 3) of periodic 3D solves, edges log-uniform in
+    [32, 256], tolerances from {1e-6, 1e-8, 1e-10}, smooth/stiff mix,
+    continuous batching under an HBM budget; latency = completion - arrival."""
+    import threading as th
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+    from paper_1504_05869_gb300.workloads import serving_trace
+    trace = serving_trace(args.requests, rate_hz=args.rate, seed=3)
+    rhos = [torch.from_numpy(rq.rho()).cuda() for rq in trace]
+    phis = [torch.zeros_like(r) for r in rhos]
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    ctx = pk.Context("D3Q111", 5, precision=args.precision, check_every=SWEEPS_PER_STEP,
+                     hbm_budget_bytes=int(args.budget_gb * 1e9), variant=-1, threaded=True,
+                     stream=stream)
+    tickets = [None] * len(trace)
+    t0 = time.perf_counter()
+
+    def feeder():
+        for k, rq in enumerate(trace):
+            delay = rq.arrival_s - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = ctx.submit(rhos[k], phis[k], knudsen=KN, tol=rq.tol,
+                                    tol_kind="rel_l2", max_sweeps=50000)
+
+    f = th.Thread(target=feeder)
+    f.start()
+    f.join()
+    lat, sw, rcs = [], [], []
+    for t in tickets:
+        rc, st = ctx.wait(t)
+        rcs.append(rc)
+        lat.append(st["wall_ms"] / 1e3)
+        sw.append(st["sweeps"])
+    dt = time.perf_counter() - t0
+    info = ctx.info()
+    ctx.close()
+    offered = len(trace) / max(trace[-1].arrival_s, 1e-9)
+    line = {"metric": "served solves/s with p50/p99 latency", "workload": "serve",
+            "value": len(trace) / dt, "unit": "solves/s",
+            "p50_latency_s": _pct(lat, 50), "p99_latency_s": _pct(lat, 99),
+            "offered_rate_hz": offered, "requests": len(trace), "seconds": dt,
+            "ok": sum(1 for r in rcs if r == 0), "statuses": sorted(set(rcs)),
+            "glups": info["site_updates"] / dt / 1e9, "precision": args.precision,
+            "hbm_budget_gb": args.budget_gb, "check_every": SWEEPS_PER_STEP,
+            "data": "synthetic",
+            "config": {"arrivals": f"Poisson {args.rate}/s, seed 3", "edges": "[32,256]",
+                       "tols": [1e-6, 1e-8, 1e-10], "lattice": "D3Q111", "knudsen": KN}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_poisson2d(args):
+    """64x64 periodic, rho = sin(2 pi x/64) sin(2 pi y/64), D2Q169 N=7, Kn 0.1,
+    stop at max |dPhi| < 1e-12; also at the paper's tau_lb = 1."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+    from paper_1504_05869_gb300.workloads import sinusoid
+    rho = sinusoid((64, 64))
+    k = 2 * np.pi / 64
+    exact = rho / (2 * k * k)
+    out = {}
+    for label, kw in (("kn0.1", {"knudsen": 0.1}), ("tau1", {"tau_lb": 1.0})):
+        r = torch.from_numpy(rho).cuda()
+        phi = torch.empty_like(r)
+        prob = pk.problem("D2Q169", (64, 64), 7, tol=1e-12, tol_kind="max_abs", check_every=1,
+                          max_sweeps=100000, **kw)
+        pk.solve(r, phi, prob)   # warm-up (module load, first launches)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = pk.solve(r, phi, prob)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        got = phi.cpu().numpy()
+        out[label] = {"status": rc, "sweeps": st["sweeps"], "seconds": dt,
+                      "glups": 4096 * st["launches"] / dt / 1e9, "tau_lb": st["tau_lb"],
+                      "rel_l2_vs_analytic": float(np.linalg.norm(got - exact) /
+                                                  np.linalg.norm(exact))}
+    line = {"metric": "time to max|dPhi| < 1e-12, 2D 64^2 D2Q169 N=7", "workload": "poisson2d",
+            "value": out["kn0.1"]["seconds"], "unit": "s", "higher_is_better": False,
+            "runs": out, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -325,7 +472,20 @@ def main():
     ap.add_argument("--lattice", default="D3Q111", choices=["D3Q111", "D3Q19"])
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "batch", "serve", "poisson2d"])
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--tol", type=float, default=0.0)
     args = ap.parse_args()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
+    if args.workload == "poisson2d":
+        return run_poisson2d(args)
     configure(args)
     if args.impl == "reference":
         return run_reference(args)
