@@ -460,6 +460,78 @@ def run_poisson2d(args):
     return 0
 
 
+def run_precision(args):
+    """Storage precision: (1) sweep throughput of binary64 and binary32
+    storage at 512^3 (256 Gaussians, sigma 1.5, seed 1); (2) time to a
+    solution within 1e-8 (rel L2) of the binary64 fixed point at 256^3
+    (64 Gaussians, sigma 2, seed 0, Kn 0.2): plain binary64 vs the mixed
+    ladder (binary32 steps, then binary64 from the converted state) vs
+    binary32 alone, each result's error against a tightly converged binary64
+    reference."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+    from paper_1504_05869_gb300.workloads import stiff_source
+    out = {"throughput_512": {}, "time_to_1e-8_256": {}}
+    if not args.no_512:
+        rho, _ = stiff_source((512, 512, 512), count=256, sigma=1.5, seed=1)
+        r = torch.from_numpy(rho).cuda()
+        del rho
+        for prec in ("fp32", "fp64"):
+            stream = torch.cuda.Stream()
+            prob = pk.problem("D3Q111", r.shape, 5, knudsen=KN, max_sweeps=10 ** 6,
+                              precision=prec)
+            with pk.Plan(prob, stream=stream) as P:
+                P.load_source(r)
+                P.sweeps(2)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.sweeps(8)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 8
+            es = 8 if prec == "fp64" else 4
+            out["throughput_512"][prec] = {"ms_per_sweep": ms, "glups": r.numel() / ms / 1e6,
+                                           "gbs": r.numel() * (2 * 111 * es + es) / ms / 1e6}
+            torch.cuda.empty_cache()
+        del r
+        torch.cuda.empty_cache()
+    rho, _ = stiff_source(SHAPE, count=64, sigma=2.0, seed=0)
+    r = torch.from_numpy(rho).cuda()
+
+    def solve(prec, tol):
+        phi = torch.empty_like(r)
+        prob = pk.problem("D3Q111", SHAPE, 5, knudsen=KN, tol=tol, tol_kind="rel_l2",
+                          check_every=SWEEPS_PER_STEP, max_sweeps=200000, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = pk.solve(r, phi, prob)
+        torch.cuda.synchronize()
+        return phi, rc, st, time.perf_counter() - t0
+
+    ref, rc, st, dt = solve("fp64", 1e-13)
+    out["reference"] = {"precision": "fp64", "tol": 1e-13, "sweeps": st["sweeps"],
+                        "seconds": dt, "status": rc}
+    nref = torch.linalg.norm(ref).item()
+    for label, prec, tol in (("fp64", "fp64", args.target_tol), ("mixed", "mixed", args.target_tol),
+                             ("fp32", "fp32", 1e-7)):
+        phi, rc, st, dt = solve(prec, tol)
+        err = (torch.linalg.norm(phi - ref).item() / nref)
+        out["time_to_1e-8_256"][label] = {"seconds": dt, "sweeps": st["sweeps"],
+                                          "launches": st["launches"], "status": rc,
+                                          "tol": tol, "rel_l2_vs_fp64_fixed_point": err}
+    t64 = out["time_to_1e-8_256"]["fp64"]["seconds"]
+    tmx = out["time_to_1e-8_256"]["mixed"]["seconds"]
+    line = {"metric": "time to rel L2 1e-8 of the binary64 fixed point, mixed vs plain binary64",
+            "workload": "precision", "value": tmx, "unit": "s", "higher_is_better": False,
+            "plain_fp64_s": t64, "speedup_vs_plain_fp64": t64 / tmx, **out,
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -473,7 +545,9 @@ def main():
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "batch", "serve", "poisson2d"])
+                    choices=["sweep", "batch", "serve", "poisson2d", "precision"])
+    ap.add_argument("--no-512", action="store_true")
+    ap.add_argument("--target-tol", type=float, default=1e-10)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -486,6 +560,8 @@ def main():
         return run_serve(args)
     if args.workload == "poisson2d":
         return run_poisson2d(args)
+    if args.workload == "precision":
+        return run_precision(args)
     configure(args)
     if args.impl == "reference":
         return run_reference(args)

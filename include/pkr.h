@@ -62,8 +62,16 @@ typedef enum pkr_lattice {
 
 /* Storage of the populations.  FP64: stored and updated in binary64.
  * FP32: stored and updated in binary32 (Phi, residual norms and the source
- * mean stay binary64). */
-typedef enum pkr_precision { PKR_FP64 = 0, PKR_FP32 = 1 } pkr_precision;
+ * mean stay binary64); the per-step change of Phi bottoms out near 1e-7 of
+ * Phi, so binary32 alone cannot meet tighter tolerances.
+ * MIXED (pkr_solve only): binary32 steps until the per-step change falls
+ * below PKR_MIXED_SWITCH_TOL (or tol, if looser), then the state is
+ * converted to binary64 and binary64 steps continue to tol.  The binary64
+ * iteration converges to the binary64 fixed point from any start, so the
+ * result meets tol as a pure binary64 solve would, at binary32 cost for the
+ * early decades. */
+typedef enum pkr_precision { PKR_FP64 = 0, PKR_FP32 = 1, PKR_MIXED = 2 } pkr_precision;
+#define PKR_MIXED_SWITCH_TOL 1e-6
 
 /* Stopping rule: change of Phi over one step, checked every check_every
  * steps.  MAX_ABS: max_x |Phi^t - Phi^(t-1)|.  REL_L2: ||dPhi||_2/||Phi^t||_2. */
@@ -166,6 +174,12 @@ int pkr_plan_run(pkr_plan *plan, int64_t steps, double tol, int tol_kind, int ch
  * Synchronises. */
 int pkr_plan_autotune(pkr_plan *plan, int steps_per_variant, int32_t *best_variant,
                       double *best_ms_per_step);
+
+/* Continue from another plan's state: copy (converting the storage type) the
+ * populations and Phi of `from`, which must have the same lattice, order and
+ * grid, and take over its step count.  Both plans must have loaded the same
+ * source (the receiving plan keeps its own S).  Synchronises. */
+int pkr_plan_import(pkr_plan *plan, const pkr_plan *from);
 
 /* Queue `count` plain steps (no residual, no synchronisation).  For timing. */
 int pkr_plan_sweeps(pkr_plan *plan, int64_t count);

@@ -10,11 +10,11 @@ from __future__ import annotations
 import ctypes
 
 from . import _pkr
-from ._pkr import (LATTICE_DIM, LATTICES, PKR_EBUSY, PKR_FP32, PKR_FP64,  # noqa: F401
+from ._pkr import (LATTICE_DIM, LATTICES, PKR_EBUSY, PKR_FP32, PKR_FP64, PKR_MIXED,  # noqa: F401
                    PKR_TOL_MAX_ABS_DPHI, PKR_TOL_REL_L2_DPHI, PkrError, check, pkr_ctx_config,
                    pkr_problem, pkr_stats)
 
-PRECISIONS = {"fp64": PKR_FP64, "fp32": PKR_FP32}
+PRECISIONS = {"fp64": PKR_FP64, "fp32": PKR_FP32, "mixed": PKR_MIXED}
 TOL_KINDS = {"max_abs": PKR_TOL_MAX_ABS_DPHI, "rel_l2": PKR_TOL_REL_L2_DPHI}
 
 
@@ -119,6 +119,9 @@ class Plan:
         check(_pkr.pkr_plan_autotune(self._h, int(steps_per_variant), ctypes.byref(best),
                                      ctypes.byref(ms)), "pkr_plan_autotune")
         return best.value, ms.value
+
+    def import_state(self, other: "Plan"):
+        check(_pkr.pkr_plan_import(self._h, other._h), "pkr_plan_import")
 
     def sweeps(self, count):
         check(_pkr.pkr_plan_sweeps(self._h, int(count)), "pkr_plan_sweeps")

@@ -21,7 +21,7 @@ LATTICES = {"D1Q5": 0, "D1Q9": 1, "D1Q13": 2, "D2Q25": 3, "D2Q81": 4, "D2Q169": 
 LATTICE_DIM = {"D1Q5": 1, "D1Q9": 1, "D1Q13": 1, "D2Q25": 2, "D2Q81": 2, "D2Q169": 2,
                "D3Q19": 3, "D3Q111": 3}
 # pkr_precision / pkr_tol_kind
-PKR_FP64, PKR_FP32 = 0, 1
+PKR_FP64, PKR_FP32, PKR_MIXED = 0, 1, 2
 PKR_TOL_MAX_ABS_DPHI, PKR_TOL_REL_L2_DPHI = 0, 1
 
 # Every symbol include/pkr.h declares (checked by the tests).
@@ -31,7 +31,7 @@ EXPORTS = [
     "pkr_plan_run", "pkr_plan_sweeps", "pkr_plan_phi", "pkr_plan_steps",
     "pkr_plan_populations", "pkr_solve", "pkr_residual_noalloc", "pkr_variant_count",
     "pkr_plan_autotune", "pkr_ctx_create", "pkr_submit", "pkr_poll", "pkr_ctx_run",
-    "pkr_ctx_wait", "pkr_ctx_info", "pkr_ctx_destroy",
+    "pkr_ctx_wait", "pkr_ctx_info", "pkr_ctx_destroy", "pkr_plan_import",
 ]
 
 
@@ -99,6 +99,7 @@ _SIGS = {
     "pkr_ctx_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(pkr_stats)]),
     "pkr_ctx_info": (ctypes.c_int, [_P, _I64, _D, _I64, ctypes.POINTER(ctypes.c_size_t), _I32]),
     "pkr_ctx_destroy": (ctypes.c_int, [_P]),
+    "pkr_plan_import": (ctypes.c_int, [_P, _P]),
 }
 
 _lib = None
@@ -165,3 +166,4 @@ pkr_ctx_run = _fn("pkr_ctx_run")
 pkr_ctx_wait = _fn("pkr_ctx_wait")
 pkr_ctx_info = _fn("pkr_ctx_info")
 pkr_ctx_destroy = _fn("pkr_ctx_destroy")
+pkr_plan_import = _fn("pkr_plan_import")

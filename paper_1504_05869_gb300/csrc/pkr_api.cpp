@@ -82,6 +82,7 @@ int validate(const pkr_problem* p, LatticeInfo* li, double* tau)
     if (!p) return PKR_EINVAL;
     if (p->dim < 1 || p->dim > 3) return PKR_EINVAL;
     if (p->precision != PKR_FP64 && p->precision != PKR_FP32) return PKR_EINVAL;
+    // (PKR_MIXED is resolved by pkr_solve into a binary32 and a binary64 plan)
     int rc = build_lattice(p->lattice, p->order, li);
     if (rc != PKR_OK) return rc;
     if (li->dim != p->dim) return PKR_EINVAL;
@@ -464,6 +465,26 @@ int pkr_plan_autotune(pkr_plan* P, int steps_per_variant, int32_t* best_variant,
     return PKR_OK;
 }
 
+int pkr_plan_import(pkr_plan* P, const pkr_plan* F)
+{
+    if (!P || !F || !F->loaded || !P->loaded) return PKR_EINVAL;
+    if (P->prob.lattice != F->prob.lattice || P->prob.order != F->prob.order ||
+        P->prob.n[0] != F->prob.n[0] || P->prob.n[1] != F->prob.n[1] ||
+        P->prob.n[2] != F->prob.n[2])
+        return PKR_EINVAL;
+    PKR_CK(cudaStreamSynchronize(F->stream));
+    const int64_t n = (int64_t)P->lat.Q * P->V;
+    if (launch_convert(F->pop[F->cur], F->prob.precision, P->pop[P->cur], P->prob.precision, n,
+                       P->stream) != 0)
+        return PKR_ECUDA;
+    PKR_CK(cudaMemcpyAsync(P->Phi, F->Phi, (size_t)P->V * 8, cudaMemcpyDeviceToDevice,
+                           P->stream));
+    PKR_CK(cudaStreamSynchronize(P->stream));
+    P->launches = F->launches;
+    P->last_residual = F->last_residual;
+    return PKR_OK;
+}
+
 int pkr_plan_sweeps(pkr_plan* P, int64_t count)
 {
     if (!P || !P->loaded || count < 0) return PKR_EINVAL;
@@ -544,10 +565,13 @@ void* pkr_plan_populations(pkr_plan* P) { return P ? P->pop[P->cur] : nullptr; }
 int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buffers,
               pkr_stats* st, void* stream)
 {
-    if (!rho || !phi) return PKR_EINVAL;
+    if (!p || !rho || !phi) return PKR_EINVAL;
     const double t0 = now_ms();
+    const bool mixed = p->precision == PKR_MIXED;
+    pkr_problem p1 = *p;
+    if (mixed) p1.precision = PKR_FP32;
     pkr_plan* P = nullptr;
-    int rc = pkr_plan_create(p, stream, &P);
+    int rc = pkr_plan_create(&p1, stream, &P);
     if (rc != PKR_OK) return rc;
     rc = pkr_plan_load_source(P, rho, host_buffers);
     if (rc != PKR_OK) {
@@ -555,7 +579,41 @@ int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buf
         return rc;
     }
     pkr_stats s{};
-    rc = pkr_plan_run(P, p->max_sweeps, p->tol, p->tol_kind, p->check_every, &s);
+    int64_t launches_total = 0;
+    double upd_bytes = 0.0;
+    if (mixed) {
+        // binary32 phase: to the switch tolerance (or tol, if looser)
+        const double tsw = p->tol > PKR_MIXED_SWITCH_TOL ? p->tol : PKR_MIXED_SWITCH_TOL;
+        rc = pkr_plan_run(P, p->max_sweeps, p->tol > 0.0 ? tsw : 0.0, p->tol_kind,
+                          p->check_every, &s);
+        const int64_t l32 = P->launches;
+        upd_bytes += (double)l32 * (double)P->V * (2.0 * P->lat.Q * 4 + 4);
+        if (rc == PKR_OK && p->tol > 0.0 && !(s.residual >= 0.0 && s.residual < p->tol)) {
+            // binary64 phase from the converted state
+            pkr_problem p2 = *p;
+            p2.precision = PKR_FP64;
+            pkr_plan* P2 = nullptr;
+            rc = pkr_plan_create(&p2, stream, &P2);
+            if (rc == PKR_OK) rc = pkr_plan_load_source(P2, rho, host_buffers);
+            if (rc == PKR_OK) rc = pkr_plan_import(P2, P);
+            if (rc == PKR_OK) {
+                pkr_plan_destroy(P);
+                P = P2;
+                const int64_t left = p->max_sweeps - (l32 - 1);
+                rc = left > 0 ? pkr_plan_run(P, left, p->tol, p->tol_kind, p->check_every, &s)
+                              : PKR_OK;
+                upd_bytes += (double)(P->launches - l32) * (double)P->V *
+                             (2.0 * P->lat.Q * 8 + 8);
+            } else if (P2) {
+                pkr_plan_destroy(P2);
+            }
+        }
+        launches_total = P->launches;
+    } else {
+        rc = pkr_plan_run(P, p->max_sweeps, p->tol, p->tol_kind, p->check_every, &s);
+        launches_total = P->launches;
+        upd_bytes = (double)launches_total * (double)P->V * (2.0 * P->lat.Q * P->elem + P->elem);
+    }
     if (rc == PKR_OK && p->tol > 0.0 && !(s.residual >= 0.0 && s.residual < p->tol))
         rc = PKR_ENOCONV;
     if (rc == PKR_OK || rc == PKR_ENOCONV) {
@@ -565,10 +623,11 @@ int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buf
     const double ms = now_ms() - t0;
     if (st) {
         *st = s;
+        st->sweeps = P->launches - 1;
+        st->launches = launches_total;
         st->wall_ms = ms;
-        const double upd = (double)(P->launches) * (double)P->V;
-        st->glups = ms > 0 ? upd / (ms * 1e6) : 0.0;
-        st->hbm_gbs = ms > 0 ? upd * (2.0 * P->lat.Q * P->elem + P->elem) / (ms * 1e6) : 0.0;
+        st->glups = ms > 0 ? (double)launches_total * (double)P->V / (ms * 1e6) : 0.0;
+        st->hbm_gbs = ms > 0 ? upd_bytes / (ms * 1e6) : 0.0;
     }
     pkr_plan_destroy(P);
     return rc;

@@ -93,5 +93,7 @@ int launch_batch_step(int lattice, int precision, int variant, BatchState* state
 int batch_occupancy(int lattice, int precision, int variant, int* blocks_per_sm);
 int launch_batch_reduce(BatchState* state, int max_grids, int grid_stride_bytes, void* stream);
 int launch_batch_increment(BatchState* state, void* stream);
+int launch_convert(const void* in, int in_precision, void* out, int out_precision, int64_t n,
+                   void* stream);
 
 }  // namespace pkr

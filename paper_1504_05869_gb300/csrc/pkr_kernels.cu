@@ -168,6 +168,15 @@ batch_reduce_kernel(const BatchState* st, int stride_bytes)
 
 __global__ void batch_step_increment_kernel(BatchState* st) { st->step += 1; }
 
+// Population storage conversion (binary32 -> binary64 or back), n elements.
+template <typename TI, typename TO>
+__global__ void convert_kernel(const TI* __restrict__ in, TO* __restrict__ out, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = (TO)in[i];
+}
+
 }  // namespace
 
 int launch_batch_reduce(BatchState* state, int max_grids, int grid_stride_bytes, void* stream)
@@ -180,6 +189,25 @@ int launch_batch_reduce(BatchState* state, int max_grids, int grid_stride_bytes,
 int launch_batch_increment(BatchState* state, void* stream)
 {
     batch_step_increment_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(state);
+    return (int)cudaGetLastError();
+}
+
+int launch_convert(const void* in, int in_precision, void* out, int out_precision, int64_t n,
+                   void* stream)
+{
+    const int blocks = 152 * 16;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (in_precision == PKR_FP32 && out_precision == PKR_FP64)
+        convert_kernel<float, double><<<blocks, 256, 0, st>>>(static_cast<const float*>(in),
+                                                              static_cast<double*>(out), n);
+    else if (in_precision == PKR_FP64 && out_precision == PKR_FP32)
+        convert_kernel<double, float><<<blocks, 256, 0, st>>>(static_cast<const double*>(in),
+                                                              static_cast<float*>(out), n);
+    else if (in_precision == out_precision)
+        return (int)cudaMemcpyAsync(out, in, (size_t)n * (in_precision == PKR_FP64 ? 8 : 4),
+                                    cudaMemcpyDeviceToDevice, st);
+    else
+        return (int)cudaErrorInvalidValue;
     return (int)cudaGetLastError();
 }
 

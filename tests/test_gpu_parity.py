@@ -274,3 +274,42 @@ def test_autotune_advances_real_steps(pk):
         P.phi(out)
     ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.2, max_steps=t + 3).phi
     assert _rel(out.cpu().numpy(), ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("src_prec,bar", [("fp64", FP64_TOL), ("fp32", 2e-5)])
+def test_plan_import_continues_state(pk, src_prec, bar):
+    import torch
+    rho = _rand((10, 9, 12), 15)
+    r = torch.from_numpy(rho).cuda()
+    out = torch.empty_like(r)
+    p1 = pk.problem("D3Q111", rho.shape, 5, tau_lb=1.2, max_sweeps=100, precision=src_prec)
+    p2 = pk.problem("D3Q111", rho.shape, 5, tau_lb=1.2, max_sweeps=100, precision="fp64")
+    with pk.Plan(p1) as A, pk.Plan(p2) as B:
+        A.load_source(r)
+        A.run(7)
+        B.load_source(r)
+        B.import_state(A)
+        assert B.steps() == 7
+        B.run(5)
+        B.phi(out)
+    ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.2, max_steps=12).phi
+    assert _rel(out.cpu().numpy(), ref) <= bar
+
+
+def test_mixed_precision_reaches_binary64_fixed_point(pk):
+    """binary32 steps, then binary64 from the converted state: the result sits
+    as close to the scheme's fixed point as a binary64 solve to the same
+    tolerance (binary32 alone cannot get below ~1e-7)."""
+    shape = (12, 10, 14)
+    rho, _ = stiff_source(shape, count=6, sigma=1.5, seed=16)
+    star = oracle.solve(rho, "D3Q111", 5, tau_lb=1.3, tol=1e-15, tol_kind=1,
+                        check_every=8, max_steps=400000).phi
+    # error ~ 1.5e3 x the per-step change on this grid (slowest mode), so a
+    # 1e-12 stopping tolerance leaves ~1.5e-9 against the fixed point
+    got, rc, st = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-12, precision="mixed",
+                             max_sweeps=400000)
+    g64, rc64, st64 = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-12, max_sweeps=400000)
+    assert rc == 0 and rc64 == 0 and st["residual"] < 1e-12
+    e_mixed, e64 = _rel(got, star), _rel(g64, star)
+    assert e_mixed < 5e-9 and e64 < 5e-9
+    assert e_mixed < 3 * e64 + 1e-12
