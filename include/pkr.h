@@ -63,7 +63,9 @@ typedef enum pkr_lattice {
 /* Storage of the populations.  FP64: stored and updated in binary64.
  * FP32: stored and updated in binary32 (Phi, residual norms and the source
  * mean stay binary64); the per-step change of Phi bottoms out near 1e-7 of
- * Phi, so binary32 alone cannot meet tighter tolerances.
+ * Phi, so binary32 alone cannot meet tighter tolerances.  binary32 rounding
+ * does not conserve the mass sum_x Phi; plans remove the drift at every
+ * residual check (through the source of the next step).
  * MIXED (pkr_solve only): binary32 steps until the per-step change falls
  * below PKR_MIXED_SWITCH_TOL (or tol, if looser), then the state is
  * converted to binary64 and binary64 steps continue to tol.  The binary64
@@ -178,7 +180,10 @@ int pkr_plan_autotune(pkr_plan *plan, int steps_per_variant, int32_t *best_varia
 /* Continue from another plan's state: copy (converting the storage type) the
  * populations and Phi of `from`, which must have the same lattice, order and
  * grid, and take over its step count.  Both plans must have loaded the same
- * source (the receiving plan keeps its own S).  Synchronises. */
+ * source (the receiving plan keeps its own S).  The copied state is projected
+ * onto the zero-mass gauge (mean of Phi removed through the k = 0
+ * equilibrium mode), which the exact iteration from zero keeps to rounding.
+ * Synchronises. */
 int pkr_plan_import(pkr_plan *plan, const pkr_plan *from);
 
 /* Queue `count` plain steps (no residual, no synchronisation).  For timing. */

@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "pkr_internal.h"
 
@@ -115,6 +116,7 @@ struct pkr_plan {
     pkr_problem prob;
     LatticeInfo lat;
     double tau_lb, omega, scale, rho_mean, last_residual, last_res3[3];
+    double soff_next;   // source offset for the next launch (mass correction)
     cudaStream_t stream;
     int device, grid, red_blocks, elem, small, variant, nsm;
     int64_t ntiles;
@@ -124,9 +126,9 @@ struct pkr_plan {
     void* S;
     double* Phi;
     double* partials;
-    double* scal;   // [0] mean, [1..3] residual out
+    double* scal;   // [0] source mean, [1..4] residual out, [5] mean of an imported Phi
     int* flag;
-    double* host;   // pinned: [0] mean, [1..3] residual, [4] flag (as int)
+    double* host;   // pinned: [0] mean, [1..4] residual, [5] import mean, [6] flag (int)
     bool loaded;
     Coefs<double> c64;
     Coefs<float> c32;
@@ -150,6 +152,8 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
     a.mode = mode;
     a.zero_in = zero_in ? 1 : 0;
     a.small = P->small;
+    a.soff = P->soff_next;
+    P->soff_next = 0.0;
     const void* c = P->prob.precision == PKR_FP64 ? (const void*)&P->c64 : (const void*)&P->c32;
     int rc = 0;
     const int pr = P->prob.precision;
@@ -213,7 +217,7 @@ size_t plan_bytes(const pkr_problem* p, const LatticeInfo& li, int64_t V, int gr
     size_t b = 2 * (size_t)li.Q * (size_t)V * e;   // ping-pong populations
     b += (size_t)V * e;                             // S
     b += (size_t)V * 8;                             // Phi
-    b += (size_t)(3 * grid_max + 4096) * 8 + 64;    // partials + scalars + flag
+    b += (size_t)(4 * grid_max + 4096) * 8 + 64;    // partials + scalars + flag
     return b;
 }
 
@@ -355,7 +359,7 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
         delete P;
         return PKR_ENOMEM;
     }
-    const size_t nscratch = (size_t)3 * kMaxGridBlocks;
+    const size_t nscratch = (size_t)4 * kMaxGridBlocks;
     bool ok = cudaMalloc(&P->pop[0], popb) == cudaSuccess &&
               cudaMalloc(&P->pop[1], popb) == cudaSuccess &&
               cudaMalloc(&P->S, (size_t)P->V * P->elem) == cudaSuccess &&
@@ -404,10 +408,10 @@ int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
         launch_make_source(rd, P->scal, P->scale, P->V, P->S, P->prob.precision, P->stream) != 0)
         return PKR_ECUDA;
     PKR_CK(cudaMemcpyAsync(P->host, P->scal, 8, cudaMemcpyDeviceToHost, P->stream));
-    PKR_CK(cudaMemcpyAsync(P->host + 4, P->flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    PKR_CK(cudaMemcpyAsync(P->host + 6, P->flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
     PKR_CK(cudaStreamSynchronize(P->stream));
     int bad = 0;
-    std::memcpy(&bad, P->host + 4, sizeof(int));
+    std::memcpy(&bad, P->host + 6, sizeof(int));
     if (bad) {
         P->loaded = false;
         return PKR_EINVAL;
@@ -418,6 +422,7 @@ int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
     P->launches = 0;
     P->cur = 0;
     P->last_residual = -1.0;
+    P->soff_next = 0.0;
     int rc = launch_one(P, kWritePhi, true);
     if (rc != PKR_OK) return rc;
     P->loaded = true;
@@ -473,15 +478,30 @@ int pkr_plan_import(pkr_plan* P, const pkr_plan* F)
         P->prob.n[2] != F->prob.n[2])
         return PKR_EINVAL;
     PKR_CK(cudaStreamSynchronize(F->stream));
-    const int64_t n = (int64_t)P->lat.Q * P->V;
-    if (launch_convert(F->pop[F->cur], F->prob.precision, P->pop[P->cur], P->prob.precision, n,
-                       P->stream) != 0)
-        return PKR_ECUDA;
+    // Project the imported state onto the zero-mass gauge: with c the mean of
+    // its latest Phi, subtract c phi_i from every population (the k = 0
+    // equilibrium mode, sum_i phi_i = 1) and c from Phi.  This removes the
+    // mass drift a binary32 run accumulates before it is continued in binary64.
     PKR_CK(cudaMemcpyAsync(P->Phi, F->Phi, (size_t)P->V * 8, cudaMemcpyDeviceToDevice,
                            P->stream));
+    if (launch_rho_partials(P->Phi, P->V, P->partials, P->red_blocks, P->flag, P->stream) != 0 ||
+        launch_finalize_mean(P->partials, P->red_blocks, P->V, P->scal + 5, P->stream) != 0)
+        return PKR_ECUDA;
+    PKR_CK(cudaMemcpyAsync(P->host + 5, P->scal + 5, 8, cudaMemcpyDeviceToHost, P->stream));
+    PKR_CK(cudaStreamSynchronize(P->stream));
+    const double c = std::isfinite(P->host[5]) ? P->host[5] : 0.0;
+    std::vector<double> shift(P->lat.Q);
+    for (int i = 0; i < P->lat.Q; ++i) shift[i] = c * P->lat.phi[i];
+    PKR_CK(cudaMemcpyAsync(P->partials, shift.data(), shift.size() * 8, cudaMemcpyHostToDevice,
+                           P->stream));
+    if (launch_convert_shift(F->pop[F->cur], F->prob.precision, P->pop[P->cur], P->prob.precision,
+                             P->lat.Q, P->V, P->partials, P->stream) != 0 ||
+        launch_make_source(P->Phi, P->scal + 5, 1.0, P->V, P->Phi, PKR_FP64, P->stream) != 0)
+        return PKR_ECUDA;
     PKR_CK(cudaStreamSynchronize(P->stream));
     P->launches = F->launches;
     P->last_residual = F->last_residual;
+    P->soff_next = 0.0;
     return PKR_OK;
 }
 
@@ -515,11 +535,18 @@ int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check
         if (rc != PKR_OK) return rc;
         ++done;
         if (mode == kCheck) {
-            PKR_CK(cudaMemcpyAsync(P->host + 1, P->scal + 1, 3 * 8, cudaMemcpyDeviceToHost,
+            PKR_CK(cudaMemcpyAsync(P->host + 1, P->scal + 1, 4 * 8, cudaMemcpyDeviceToHost,
                                    P->stream));
             PKR_CK(cudaStreamSynchronize(P->stream));
             const double r = P->host[1 + (tol_kind == PKR_TOL_MAX_ABS_DPHI ? 0 : 1)];
             P->last_residual = r;
+            // binary32 rounding does not conserve the mass sum_x Phi, and the
+            // k = 0 mode never decays, so the mass random-walks away from its
+            // exact value 0 (the source has zero mean).  Remove it in the next
+            // step through the source: sum_i chi_i = 1, so adding -M/V to S at
+            // every site removes exactly M.
+            if (P->prob.precision == PKR_FP32 && std::isfinite(P->host[4]))
+                P->soff_next = -P->host[4] / (double)P->V;
             ++nchecks;
             if (!std::isfinite(P->host[1]) || !std::isfinite(P->host[3]) ||
                 (nchecks > 2 && r > 1e6 * min_res && r > 1e-300)) {

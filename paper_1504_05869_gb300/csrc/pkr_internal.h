@@ -68,13 +68,15 @@ struct SweepArgs {
     void* B;              // populations out
     const void* S;        // source, V values of the storage type
     double* Phi;          // density buffer (binary64)
-    double* partials;     // residual partials: 3 doubles per block
+    double* partials;     // residual partials: 4 doubles per block
     int64_t V;            // sites
     int32_t nx, ny, nz;
     int32_t ntiles;       // flat tiles of 32 sites
     int32_t mode;         // SweepMode
     int32_t zero_in;      // populations in are all zero (first step)
     int32_t small;        // some edge shorter than the lattice reach
+    int32_t pad;
+    double soff;          // constant added to S in this step (mass correction)
 };
 
 
@@ -85,7 +87,7 @@ int launch_finalize_mean(const double* partials, int nblocks, int64_t V, double*
                          void* stream);
 int launch_make_source(const double* rho, const double* mean, double scale, int64_t V,
                        void* S, int precision, void* stream);
-int launch_finalize_residual(const double* partials, int nblocks, double* out3, void* stream);
+int launch_finalize_residual(const double* partials, int nblocks, double* out4, void* stream);
 
 // Batch engine kernels (sweep_*.cu / pkr_kernels.cu).
 int launch_batch_step(int lattice, int precision, int variant, BatchState* state, int check_every,
@@ -95,5 +97,9 @@ int launch_batch_reduce(BatchState* state, int max_grids, int grid_stride_bytes,
 int launch_batch_increment(BatchState* state, void* stream);
 int launch_convert(const void* in, int in_precision, void* out, int out_precision, int64_t n,
                    void* stream);
+// out[i*V + x] = in[i*V + x] - shift[i] (storage conversion with a per-plane
+// shift; shift: Q doubles in device memory).
+int launch_convert_shift(const void* in, int in_precision, void* out, int out_precision, int Q,
+                         int64_t V, const double* shift, void* stream);
 
 }  // namespace pkr

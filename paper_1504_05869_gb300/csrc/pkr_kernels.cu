@@ -79,41 +79,47 @@ __global__ void make_source_kernel(const double* __restrict__ rho, const double*
         S[i] = (T)((rho[i] - m) * scale);
 }
 
-// out3[0] = max |dPhi|, out3[1] = ||dPhi||_2 / ||Phi||_2 (0 if both vanish,
-// +inf if only Phi does), out3[2] = ||Phi||_2.
+// out4[0] = max |dPhi|, out4[1] = ||dPhi||_2 / ||Phi||_2 (0 if both vanish,
+// +inf if only Phi does), out4[2] = ||Phi||_2, out4[3] = sum Phi (the mass).
 __global__ void __launch_bounds__(kRedThreads)
-finalize_residual_kernel(const double* __restrict__ partials, int n, double* out3)
+finalize_residual_kernel(const double* __restrict__ partials, int n, double* out4)
 {
-    __shared__ double s0[kRedThreads / 32], s1[kRedThreads / 32], s2[kRedThreads / 32];
-    double d2 = 0.0, n2 = 0.0, mx = 0.0;
+    __shared__ double s0[kRedThreads / 32], s1[kRedThreads / 32], s2[kRedThreads / 32],
+        s3[kRedThreads / 32];
+    double d2 = 0.0, n2 = 0.0, mx = 0.0, ms = 0.0;
     for (int i = threadIdx.x; i < n; i += kRedThreads) {
-        d2 += partials[3 * i + 0];
-        n2 += partials[3 * i + 1];
-        mx = fmax(mx, partials[3 * i + 2]);
+        d2 += partials[4 * i + 0];
+        n2 += partials[4 * i + 1];
+        mx = fmax(mx, partials[4 * i + 2]);
+        ms += partials[4 * i + 3];
     }
     d2 = warp_sum(d2);
     n2 = warp_sum(n2);
     mx = warp_max(mx);
+    ms = warp_sum(ms);
     if ((threadIdx.x & 31) == 0) {
         s0[threadIdx.x >> 5] = d2;
         s1[threadIdx.x >> 5] = n2;
         s2[threadIdx.x >> 5] = mx;
+        s3[threadIdx.x >> 5] = ms;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0, c = 0.0;
+        double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
         for (int k = 0; k < kRedThreads / 32; ++k) {
             a += s0[k];
             b += s1[k];
             c = fmax(c, s2[k]);
+            d += s3[k];
         }
-        out3[0] = c;
-        out3[1] = (b > 0.0) ? sqrt(a) / sqrt(b) : (a == 0.0 ? 0.0 : INFINITY);
-        out3[2] = sqrt(b);
+        out4[0] = c;
+        out4[1] = (b > 0.0) ? sqrt(a) / sqrt(b) : (a == 0.0 ? 0.0 : INFINITY);
+        out4[2] = sqrt(b);
+        out4[3] = d;
         // a NaN anywhere poisons the max; report it
         if (!(a == a) || !(b == b)) {
-            out3[0] = NAN;
-            out3[1] = NAN;
+            out4[0] = NAN;
+            out4[1] = NAN;
         }
     }
 }
@@ -168,6 +174,17 @@ batch_reduce_kernel(const BatchState* st, int stride_bytes)
 
 __global__ void batch_step_increment_kernel(BatchState* st) { st->step += 1; }
 
+// Storage conversion with a per-plane shift: out[i*V + x] = in[i*V + x] - sh[i].
+template <typename TI, typename TO>
+__global__ void convert_shift_kernel(const TI* __restrict__ in, TO* __restrict__ out, int Q,
+                                     int64_t V, const double* __restrict__ sh)
+{
+    const int64_t n = (int64_t)Q * V;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
+        out[k] = (TO)((double)in[k] - sh[k / V]);
+}
+
 // Population storage conversion (binary32 -> binary64 or back), n elements.
 template <typename TI, typename TO>
 __global__ void convert_kernel(const TI* __restrict__ in, TO* __restrict__ out, int64_t n)
@@ -211,6 +228,28 @@ int launch_convert(const void* in, int in_precision, void* out, int out_precisio
     return (int)cudaGetLastError();
 }
 
+int launch_convert_shift(const void* in, int in_precision, void* out, int out_precision, int Q,
+                         int64_t V, const double* shift, void* stream)
+{
+    const int blocks = 152 * 16;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (in_precision == PKR_FP32 && out_precision == PKR_FP64)
+        convert_shift_kernel<float, double><<<blocks, 256, 0, st>>>(
+            static_cast<const float*>(in), static_cast<double*>(out), Q, V, shift);
+    else if (in_precision == PKR_FP64 && out_precision == PKR_FP64)
+        convert_shift_kernel<double, double><<<blocks, 256, 0, st>>>(
+            static_cast<const double*>(in), static_cast<double*>(out), Q, V, shift);
+    else if (in_precision == PKR_FP64 && out_precision == PKR_FP32)
+        convert_shift_kernel<double, float><<<blocks, 256, 0, st>>>(
+            static_cast<const double*>(in), static_cast<float*>(out), Q, V, shift);
+    else if (in_precision == PKR_FP32 && out_precision == PKR_FP32)
+        convert_shift_kernel<float, float><<<blocks, 256, 0, st>>>(
+            static_cast<const float*>(in), static_cast<float*>(out), Q, V, shift);
+    else
+        return (int)cudaErrorInvalidValue;
+    return (int)cudaGetLastError();
+}
+
 int launch_rho_partials(const double* rho, int64_t V, double* partials, int nblocks,
                         int* nonfinite, void* stream)
 {
@@ -240,9 +279,9 @@ int launch_make_source(const double* rho, const double* mean, double scale, int6
     return (int)cudaGetLastError();
 }
 
-int launch_finalize_residual(const double* partials, int nblocks, double* out3, void* stream)
+int launch_finalize_residual(const double* partials, int nblocks, double* out4, void* stream)
 {
-    finalize_residual_kernel<<<1, kRedThreads, 0, (cudaStream_t)stream>>>(partials, nblocks, out3);
+    finalize_residual_kernel<<<1, kRedThreads, 0, (cudaStream_t)stream>>>(partials, nblocks, out4);
     return (int)cudaGetLastError();
 }
 

@@ -262,19 +262,20 @@ struct TileGrid {
     double* Phi;    // density (written on write/check sweeps)
     int64_t V;
     int nx, ny, nz, small;
+    double soff;    // constant added to S in this step (mass correction)
 };
 
 // One 32-site tile of one grid, executed by the G warps of a tile slot:
 // pull (cp.async), density, relax + store, density output.  On check sweeps
-// the lane's contributions to |dPhi|^2, |Phi|^2 and max |dPhi| are added to
-// d2, n2, mx (velocity group 0 only).
+// the lane's contributions to |dPhi|^2, |Phi|^2, max |dPhi| and sum Phi are
+// added to d2, n2, mx, ms (velocity group 0 only).
 template <class L, typename T, int G, int TILES>
 __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
                                           const Coefs<typename AccType<T>::type>& c, int tile,
                                           int mode, bool zero_in, int lane, int grp, int sub,
                                           uint32_t sbase, long long (&xacc)[TILES][G][32],
                                           int (&xexp)[TILES][G][32], double& d2, double& n2,
-                                          double& mx)
+                                          double& mx, double& ms)
 {
     using R = typename AccType<T>::type;
     using ST = Staged<L, T, G, TILES>;
@@ -310,7 +311,7 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
         }
     }
     const int nbytes = (valid && !zero_in) ? (int)sizeof(T) : 0;
-    const R Sx = valid ? (R)tg.S[s] : R(0);
+    const R Sx = valid ? (R)((double)tg.S[s] + tg.soff) : R(0);
 
     static_for<0, G>([&](auto GI) {
         constexpr int g = decltype(GI)::value;
@@ -422,6 +423,7 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
                 d2 += d * d;
                 n2 += ph * ph;
                 mx = fmax(mx, fabs(d));
+                ms += ph;
             }
             tg.Phi[s] = ph;
         }
@@ -437,7 +439,7 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     constexpr int TILES = TILES_;
     using ST = Staged<L, T, G, TILES>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double rpart[TILES][3];
+    __shared__ double rpart[TILES][4];
     __shared__ long long xacc[TILES][G][32];   // per-group partial densities of a tile
     __shared__ int xexp[TILES][G][32];         // per-group largest exponents
 
@@ -448,13 +450,14 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(
         reinterpret_cast<T*>(smem_raw) + (size_t)wib * ST::CH * 32 + lane);
     const TileGrid<T> tg{static_cast<const T*>(a.A), static_cast<T*>(a.B),
-                         static_cast<const T*>(a.S), a.Phi, a.V, a.nx, a.ny, a.nz, a.small};
+                         static_cast<const T*>(a.S), a.Phi, a.V, a.nx, a.ny, a.nz, a.small,
+                         a.soff};
 
-    double rd2 = 0.0, rn2 = 0.0, rmx = 0.0;
+    double rd2 = 0.0, rn2 = 0.0, rmx = 0.0, rms = 0.0;
     const int nt = gridDim.x * TILES;
     for (int tile = blockIdx.x * TILES + sub; tile < a.ntiles; tile += nt)
         tile_step<L, T, G, TILES>(tg, c, tile, a.mode, a.zero_in != 0, lane, grp, sub, sbase,
-                                  xacc, xexp, rd2, rn2, rmx);
+                                  xacc, xexp, rd2, rn2, rmx, rms);
 
     if (a.mode == kCheck) {
         if (grp == 0) {
@@ -463,24 +466,28 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
                 rd2 += __shfl_down_sync(0xffffffffu, rd2, o);
                 rn2 += __shfl_down_sync(0xffffffffu, rn2, o);
                 rmx = fmax(rmx, __shfl_down_sync(0xffffffffu, rmx, o));
+                rms += __shfl_down_sync(0xffffffffu, rms, o);
             }
             if (lane == 0) {
                 rpart[sub][0] = rd2;
                 rpart[sub][1] = rn2;
                 rpart[sub][2] = rmx;
+                rpart[sub][3] = rms;
             }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
             for (int k = 0; k < TILES; ++k) {
                 t0 += rpart[k][0];
                 t1 += rpart[k][1];
                 t2 = fmax(t2, rpart[k][2]);
+                t3 += rpart[k][3];
             }
-            a.partials[3 * blockIdx.x + 0] = t0;
-            a.partials[3 * blockIdx.x + 1] = t1;
-            a.partials[3 * blockIdx.x + 2] = t2;
+            a.partials[4 * blockIdx.x + 0] = t0;
+            a.partials[4 * blockIdx.x + 1] = t1;
+            a.partials[4 * blockIdx.x + 2] = t2;
+            a.partials[4 * blockIdx.x + 3] = t3;
         }
     }
 }
@@ -536,10 +543,10 @@ sweep_batch_kernel(BatchState* st, int K)
         else if (zero_in || (age + 2) % K == 0) mode = kWritePhi;
         const TileGrid<T> tg{static_cast<const T*>(gd.pop[cur]), static_cast<T*>(gd.pop[cur ^ 1]),
                              static_cast<const T*>(gd.S), gd.Phi, gd.V, gd.nx, gd.ny, gd.nz,
-                             gd.small};
-        double d2 = 0.0, n2 = 0.0, mx = 0.0;
+                             gd.small, 0.0};
+        double d2 = 0.0, n2 = 0.0, mx = 0.0, ms = 0.0;
         tile_step<L, T, G, TILES>(tg, gd.c, tile - gd.tile_begin, mode, zero_in, lane, grp, sub,
-                                  sbase, xacc, xexp, d2, n2, mx);
+                                  sbase, xacc, xexp, d2, n2, mx, ms);
         if (mode == kCheck && grp == 0) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
