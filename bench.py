@@ -478,7 +478,7 @@ def run_precision(args):
         rho, _ = stiff_source((512, 512, 512), count=256, sigma=1.5, seed=1)
         r = torch.from_numpy(rho).cuda()
         del rho
-        for prec in ("fp32", "fp64"):
+        for prec in ("fp16", "fp32", "fp64"):
             stream = torch.cuda.Stream()
             prob = pk.problem("D3Q111", r.shape, 5, knudsen=KN, max_sweeps=10 ** 6,
                               precision=prec)
@@ -492,9 +492,11 @@ def run_precision(args):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / 8
-            es = 8 if prec == "fp64" else 4
+            es = {"fp64": 8, "fp32": 4, "fp16": 2}[prec]
+            ss = 8 if prec == "fp64" else 4
             out["throughput_512"][prec] = {"ms_per_sweep": ms, "glups": r.numel() / ms / 1e6,
-                                           "gbs": r.numel() * (2 * 111 * es + es) / ms / 1e6}
+                                           "gbs": r.numel() * (2 * 111 * es + ss) / ms / 1e6,
+                                           "bytes_per_site": 2 * 111 * es + ss}
             torch.cuda.empty_cache()
         del r
         torch.cuda.empty_cache()
@@ -516,14 +518,16 @@ def run_precision(args):
                         "seconds": dt, "status": rc}
     nref = torch.linalg.norm(ref).item()
     for label, prec, tol in (("fp64", "fp64", args.target_tol), ("mixed", "mixed", args.target_tol),
-                             ("fp32", "fp32", 1e-7)):
+                             ("mixed16", "mixed16", args.target_tol), ("fp32", "fp32", 1e-7),
+                             ("fp16", "fp16", 1e-3)):
         phi, rc, st, dt = solve(prec, tol)
         err = (torch.linalg.norm(phi - ref).item() / nref)
         out["time_to_1e-8_256"][label] = {"seconds": dt, "sweeps": st["sweeps"],
                                           "launches": st["launches"], "status": rc,
                                           "tol": tol, "rel_l2_vs_fp64_fixed_point": err}
     t64 = out["time_to_1e-8_256"]["fp64"]["seconds"]
-    tmx = out["time_to_1e-8_256"]["mixed"]["seconds"]
+    tmx = min(out["time_to_1e-8_256"]["mixed"]["seconds"],
+              out["time_to_1e-8_256"]["mixed16"]["seconds"])
     line = {"metric": "time to rel L2 1e-8 of the binary64 fixed point, mixed vs plain binary64",
             "workload": "precision", "value": tmx, "unit": "s", "higher_is_better": False,
             "plain_fp64_s": t64, "speedup_vs_plain_fp64": t64 / tmx, **out,
@@ -543,7 +547,7 @@ def main():
     ap.add_argument("--size", type=int, default=0, help="cube edge (default 256)")
     ap.add_argument("--lattice", default="D3Q111", choices=["D3Q111", "D3Q19"])
     ap.add_argument("--order", type=int, default=5)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16"])
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "batch", "serve", "poisson2d", "precision"])
     ap.add_argument("--no-512", action="store_true")

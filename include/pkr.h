@@ -71,9 +71,17 @@ typedef enum pkr_lattice {
  * converted to binary64 and binary64 steps continue to tol.  The binary64
  * iteration converges to the binary64 fixed point from any start, so the
  * result meets tol as a pure binary64 solve would, at binary32 cost for the
- * early decades. */
-typedef enum pkr_precision { PKR_FP64 = 0, PKR_FP32 = 1, PKR_MIXED = 2 } pkr_precision;
+ * early decades.
+ * FP16: populations stored in binary16 with a power-of-two scale per array
+ * (set before each step so that the step's largest value has 4x headroom),
+ * arithmetic in binary32, source in binary32; accurate to ~1e-4 of Phi.
+ * MIXED16 (pkr_solve only): binary16 to PKR_MIXED16_SWITCH_TOL, binary32 to
+ * PKR_MIXED_SWITCH_TOL, then binary64 to tol. */
+typedef enum pkr_precision {
+    PKR_FP64 = 0, PKR_FP32 = 1, PKR_MIXED = 2, PKR_FP16 = 3, PKR_MIXED16 = 4
+} pkr_precision;
 #define PKR_MIXED_SWITCH_TOL 1e-6
+#define PKR_MIXED16_SWITCH_TOL 1e-3
 
 /* Stopping rule: change of Phi over one step, checked every check_every
  * steps.  MAX_ABS: max_x |Phi^t - Phi^(t-1)|.  REL_L2: ||dPhi||_2/||Phi^t||_2. */

@@ -19,6 +19,8 @@ namespace pkr {
 template <class L, typename T> int launch_sweep_t(int, const SweepArgs&, const void*, int, void*);
 template <class L, typename T> int occupancy_t(int, int*, int*);
 template <class L> int variant_count_t();
+template <class L> int launch_sweep_h16(const SweepArgs&, const void*, int, void*);
+template <class L> int occupancy_h16(int*, int*);
 }  // namespace pkr
 
 #define PKR_CK(call)                                     \
@@ -70,7 +72,13 @@ int default_variant(int lattice, int precision)
     return variant_count(lattice) > 2 ? 2 : 0;
 }
 
-int elem_bytes(int precision) { return precision == PKR_FP64 ? 8 : 4; }
+int elem_bytes(int precision)
+{
+    return precision == PKR_FP64 ? 8 : precision == PKR_FP32 ? 4 : 2;
+}
+// Bytes of one source value: binary64 plans keep S in binary64, the others
+// in binary32.
+int source_bytes(int precision) { return precision == PKR_FP64 ? 8 : 4; }
 
 double now_ms()
 {
@@ -82,8 +90,9 @@ int validate(const pkr_problem* p, LatticeInfo* li, double* tau)
 {
     if (!p) return PKR_EINVAL;
     if (p->dim < 1 || p->dim > 3) return PKR_EINVAL;
-    if (p->precision != PKR_FP64 && p->precision != PKR_FP32) return PKR_EINVAL;
-    // (PKR_MIXED is resolved by pkr_solve into a binary32 and a binary64 plan)
+    if (p->precision != PKR_FP64 && p->precision != PKR_FP32 && p->precision != PKR_FP16)
+        return PKR_EINVAL;
+    // (PKR_MIXED / PKR_MIXED16 are resolved by pkr_solve into a ladder of plans)
     int rc = build_lattice(p->lattice, p->order, li);
     if (rc != PKR_OK) return rc;
     if (li->dim != p->dim) return PKR_EINVAL;
@@ -128,7 +137,11 @@ struct pkr_plan {
     double* partials;
     double* scal;   // [0] source mean, [1..4] residual out, [5] mean of an imported Phi
     int* flag;
-    double* host;   // pinned: [0] mean, [1..4] residual, [5] import mean, [6] flag (int)
+    double* host;   // pinned: [0] mean, [1..4] residual, [5] import mean, [6] flag (int),
+                    // [7] binary16 overflow flag (int)
+    float* h16sc;          // binary16 storage: scales of the two arrays
+    unsigned int* h16max;  // binary16 storage: max |p| of the current step
+    int* h16of;            // binary16 storage: overflow flag
     bool loaded;
     Coefs<double> c64;
     Coefs<float> c32;
@@ -158,6 +171,32 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
     int rc = 0;
     const int pr = P->prob.precision;
     const int vr = P->variant;
+    a.cur = P->cur;
+    a.sc = P->h16sc;
+    a.pmax = P->h16max;
+    a.oflow = P->h16of;
+    if (pr == PKR_FP16) {
+        switch (P->prob.lattice) {
+        case PKR_D1Q5: rc = launch_sweep_h16<D1Q5>(a, c, P->grid, P->stream); break;
+        case PKR_D1Q9: rc = launch_sweep_h16<D1Q9>(a, c, P->grid, P->stream); break;
+        case PKR_D1Q13: rc = launch_sweep_h16<D1Q13>(a, c, P->grid, P->stream); break;
+        case PKR_D2Q25: rc = launch_sweep_h16<D2Q25>(a, c, P->grid, P->stream); break;
+        case PKR_D2Q81: rc = launch_sweep_h16<D2Q81>(a, c, P->grid, P->stream); break;
+        case PKR_D2Q169: rc = launch_sweep_h16<D2Q169>(a, c, P->grid, P->stream); break;
+        case PKR_D3Q19: rc = launch_sweep_h16<D3Q19>(a, c, P->grid, P->stream); break;
+        case PKR_D3Q111: rc = launch_sweep_h16<D3Q111>(a, c, P->grid, P->stream); break;
+        default: return PKR_EINVAL;
+        }
+        if (rc != 0) return PKR_ECUDA;
+        // the array this step read is the one the next step writes
+        if (launch_h16_rescale(P->h16sc, P->h16max, P->cur, P->stream) != 0) return PKR_ECUDA;
+        P->cur ^= 1;
+        P->launches += 1;
+        if (mode == kCheck &&
+            launch_finalize_residual(P->partials, P->grid, P->scal + 1, P->stream) != 0)
+            return PKR_ECUDA;
+        return PKR_OK;
+    }
     switch (P->prob.lattice) {
     case PKR_D1Q5: rc = dispatch_launch<D1Q5>(vr, pr, a, c, P->grid, P->stream); break;
     case PKR_D1Q9: rc = dispatch_launch<D1Q9>(vr, pr, a, c, P->grid, P->stream); break;
@@ -181,6 +220,19 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
 
 int occupancy(int variant, int lattice, int precision, int* b, int* tpb)
 {
+    if (precision == PKR_FP16) {
+        switch (lattice) {
+        case PKR_D1Q5: return occupancy_h16<D1Q5>(b, tpb);
+        case PKR_D1Q9: return occupancy_h16<D1Q9>(b, tpb);
+        case PKR_D1Q13: return occupancy_h16<D1Q13>(b, tpb);
+        case PKR_D2Q25: return occupancy_h16<D2Q25>(b, tpb);
+        case PKR_D2Q81: return occupancy_h16<D2Q81>(b, tpb);
+        case PKR_D2Q169: return occupancy_h16<D2Q169>(b, tpb);
+        case PKR_D3Q19: return occupancy_h16<D3Q19>(b, tpb);
+        case PKR_D3Q111: return occupancy_h16<D3Q111>(b, tpb);
+        }
+        return -1;
+    }
     switch (lattice) {
     case PKR_D1Q5: return dispatch_occ<D1Q5>(variant, precision, b, tpb);
     case PKR_D1Q9: return dispatch_occ<D1Q9>(variant, precision, b, tpb);
@@ -214,8 +266,8 @@ int set_variant(pkr_plan* P, int variant)
 size_t plan_bytes(const pkr_problem* p, const LatticeInfo& li, int64_t V, int grid_max)
 {
     const size_t e = (size_t)elem_bytes(p->precision);
-    size_t b = 2 * (size_t)li.Q * (size_t)V * e;   // ping-pong populations
-    b += (size_t)V * e;                             // S
+    size_t b = 2 * ((size_t)li.Q * (size_t)V * e + 16);   // ping-pong populations
+    b += (size_t)V * source_bytes(p->precision);           // S
     b += (size_t)V * 8;                             // Phi
     b += (size_t)(4 * grid_max + 4096) * 8 + 64;    // partials + scalars + flag
     return b;
@@ -338,7 +390,8 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
     P->nsm = nsm;
     P->ntiles = tiles_of(p->n);
     const int nvar = variant_count(p->lattice);
-    const int var = (p->variant >= 0) ? p->variant : default_variant(p->lattice, p->precision);
+    int var = (p->variant >= 0) ? p->variant : default_variant(p->lattice, p->precision);
+    if (p->precision == PKR_FP16) var = 0;   // one geometry for binary16 storage
     if (var >= nvar) {
         delete P;
         return PKR_EINVAL;
@@ -349,7 +402,8 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
     }
     P->red_blocks = nsm * 4;
 
-    const size_t popb = (size_t)li.Q * (size_t)P->V * (size_t)P->elem;
+    // (+16 bytes: binary16 steps read the aligned 4-byte word around a value)
+    const size_t popb = (size_t)li.Q * (size_t)P->V * (size_t)P->elem + 16;
     size_t freeb = 0, totb = 0;
     if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) {
         delete P;
@@ -362,7 +416,10 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
     const size_t nscratch = (size_t)4 * kMaxGridBlocks;
     bool ok = cudaMalloc(&P->pop[0], popb) == cudaSuccess &&
               cudaMalloc(&P->pop[1], popb) == cudaSuccess &&
-              cudaMalloc(&P->S, (size_t)P->V * P->elem) == cudaSuccess &&
+              cudaMalloc(&P->S, (size_t)P->V * source_bytes(p->precision)) == cudaSuccess &&
+              cudaMalloc((void**)&P->h16sc, 2 * sizeof(float)) == cudaSuccess &&
+              cudaMalloc((void**)&P->h16max, sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc((void**)&P->h16of, sizeof(int)) == cudaSuccess &&
               cudaMalloc((void**)&P->Phi, (size_t)P->V * 8) == cudaSuccess &&
               cudaMalloc((void**)&P->partials, nscratch * 8) == cudaSuccess &&
               cudaMalloc((void**)&P->scal, 8 * 8) == cudaSuccess &&
@@ -388,6 +445,9 @@ int pkr_plan_destroy(pkr_plan* P)
     cudaFree(P->partials);
     cudaFree(P->scal);
     cudaFree(P->flag);
+    cudaFree(P->h16sc);
+    cudaFree(P->h16max);
+    cudaFree(P->h16of);
     if (P->host) cudaFreeHost(P->host);
     delete P;
     return PKR_OK;
@@ -405,8 +465,15 @@ int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
     PKR_CK(cudaMemsetAsync(P->flag, 0, sizeof(int), P->stream));
     if (launch_rho_partials(rd, P->V, P->partials, P->red_blocks, P->flag, P->stream) != 0 ||
         launch_finalize_mean(P->partials, P->red_blocks, P->V, P->scal, P->stream) != 0 ||
-        launch_make_source(rd, P->scal, P->scale, P->V, P->S, P->prob.precision, P->stream) != 0)
+        launch_make_source(rd, P->scal, P->scale, P->V, P->S,
+                           P->prob.precision == PKR_FP64 ? PKR_FP64 : PKR_FP32, P->stream) != 0)
         return PKR_ECUDA;
+    if (P->prob.precision == PKR_FP16) {
+        PKR_CK(cudaMemsetAsync(P->h16max, 0, sizeof(unsigned int), P->stream));
+        PKR_CK(cudaMemsetAsync(P->h16of, 0, sizeof(int), P->stream));
+        if (launch_absmax_f32(static_cast<const float*>(P->S), P->V, P->h16max, P->stream) != 0)
+            return PKR_ECUDA;
+    }
     PKR_CK(cudaMemcpyAsync(P->host, P->scal, 8, cudaMemcpyDeviceToHost, P->stream));
     PKR_CK(cudaMemcpyAsync(P->host + 6, P->flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
     PKR_CK(cudaStreamSynchronize(P->stream));
@@ -417,6 +484,21 @@ int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
         return PKR_EINVAL;
     }
     P->rho_mean = P->host[0];
+    if (P->prob.precision == PKR_FP16) {
+        // scale of the first write: the step from zero stores chi_i S
+        unsigned int mb = 0;
+        PKR_CK(cudaMemcpy(&mb, P->h16max, sizeof(mb), cudaMemcpyDeviceToHost));
+        float ms = 0.f;
+        std::memcpy(&ms, &mb, sizeof(ms));
+        double mchi = 0.0;
+        for (int i = 0; i < P->lat.Q; ++i) mchi = std::fmax(mchi, std::fabs(P->lat.chi[i]));
+        const double m = (double)ms * mchi;
+        float sc = 1.0f;
+        if (m > 0.0 && std::isfinite(m)) sc = std::ldexp(1.0f, std::ilogb(4.0 * m / 65504.0) + 1);
+        const float sc2[2] = {sc, sc};
+        PKR_CK(cudaMemcpyAsync(P->h16sc, sc2, sizeof(sc2), cudaMemcpyHostToDevice, P->stream));
+        PKR_CK(cudaMemsetAsync(P->h16max, 0, sizeof(unsigned int), P->stream));
+    }
     // Phi^0 = 0; the first step starts from zero populations
     PKR_CK(cudaMemsetAsync(P->Phi, 0, (size_t)P->V * 8, P->stream));
     P->launches = 0;
@@ -494,8 +576,9 @@ int pkr_plan_import(pkr_plan* P, const pkr_plan* F)
     for (int i = 0; i < P->lat.Q; ++i) shift[i] = c * P->lat.phi[i];
     PKR_CK(cudaMemcpyAsync(P->partials, shift.data(), shift.size() * 8, cudaMemcpyHostToDevice,
                            P->stream));
+    if (P->prob.precision == PKR_FP16) return PKR_EINVAL;   // imports into binary16: no
     if (launch_convert_shift(F->pop[F->cur], F->prob.precision, P->pop[P->cur], P->prob.precision,
-                             P->lat.Q, P->V, P->partials, P->stream) != 0 ||
+                             P->lat.Q, P->V, P->partials, P->stream, F->h16sc + F->cur) != 0 ||
         launch_make_source(P->Phi, P->scal + 5, 1.0, P->V, P->Phi, PKR_FP64, P->stream) != 0)
         return PKR_ECUDA;
     PKR_CK(cudaStreamSynchronize(P->stream));
@@ -545,8 +628,16 @@ int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check
             // exact value 0 (the source has zero mean).  Remove it in the next
             // step through the source: sum_i chi_i = 1, so adding -M/V to S at
             // every site removes exactly M.
-            if (P->prob.precision == PKR_FP32 && std::isfinite(P->host[4]))
+            if (P->prob.precision != PKR_FP64 && std::isfinite(P->host[4]))
                 P->soff_next = -P->host[4] / (double)P->V;
+            if (P->prob.precision == PKR_FP16) {
+                int of = 0;
+                PKR_CK(cudaMemcpy(&of, P->h16of, sizeof(int), cudaMemcpyDeviceToHost));
+                if (of) {
+                    status = PKR_EDIVERGED;
+                    break;
+                }
+            }
             ++nchecks;
             if (!std::isfinite(P->host[1]) || !std::isfinite(P->host[3]) ||
                 (nchecks > 2 && r > 1e6 * min_res && r > 1e-300)) {
@@ -569,7 +660,7 @@ int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check
         st->wall_ms = ms;
         const double upd = (double)done * (double)P->V;
         st->glups = ms > 0 ? upd / (ms * 1e6) : 0.0;
-        const double bytes_site = 2.0 * P->lat.Q * P->elem + P->elem;
+        const double bytes_site = 2.0 * P->lat.Q * P->elem + source_bytes(P->prob.precision);
         st->hbm_gbs = ms > 0 ? upd * bytes_site / (ms * 1e6) : 0.0;
     }
     return status;
@@ -594,9 +685,23 @@ int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buf
 {
     if (!p || !rho || !phi) return PKR_EINVAL;
     const double t0 = now_ms();
-    const bool mixed = p->precision == PKR_MIXED;
+    // Precision ladder: each stage runs to its switch tolerance (or tol, if
+    // looser), then the next, wider stage continues from the converted state.
+    int stages[3];
+    double switch_tol[3];
+    int nst = 0;
+    if (p->precision == PKR_MIXED16) {
+        stages[nst] = PKR_FP16, switch_tol[nst++] = PKR_MIXED16_SWITCH_TOL;
+        stages[nst] = PKR_FP32, switch_tol[nst++] = PKR_MIXED_SWITCH_TOL;
+        stages[nst] = PKR_FP64, switch_tol[nst++] = p->tol;
+    } else if (p->precision == PKR_MIXED) {
+        stages[nst] = PKR_FP32, switch_tol[nst++] = PKR_MIXED_SWITCH_TOL;
+        stages[nst] = PKR_FP64, switch_tol[nst++] = p->tol;
+    } else {
+        stages[nst] = p->precision, switch_tol[nst++] = p->tol;
+    }
     pkr_problem p1 = *p;
-    if (mixed) p1.precision = PKR_FP32;
+    p1.precision = stages[0];
     pkr_plan* P = nullptr;
     int rc = pkr_plan_create(&p1, stream, &P);
     if (rc != PKR_OK) return rc;
@@ -606,41 +711,37 @@ int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buf
         return rc;
     }
     pkr_stats s{};
-    int64_t launches_total = 0;
     double upd_bytes = 0.0;
-    if (mixed) {
-        // binary32 phase: to the switch tolerance (or tol, if looser)
-        const double tsw = p->tol > PKR_MIXED_SWITCH_TOL ? p->tol : PKR_MIXED_SWITCH_TOL;
-        rc = pkr_plan_run(P, p->max_sweeps, p->tol > 0.0 ? tsw : 0.0, p->tol_kind,
-                          p->check_every, &s);
-        const int64_t l32 = P->launches;
-        upd_bytes += (double)l32 * (double)P->V * (2.0 * P->lat.Q * 4 + 4);
-        if (rc == PKR_OK && p->tol > 0.0 && !(s.residual >= 0.0 && s.residual < p->tol)) {
-            // binary64 phase from the converted state
-            pkr_problem p2 = *p;
-            p2.precision = PKR_FP64;
+    int64_t prev_launches = 0;
+    for (int k = 0; k < nst; ++k) {
+        if (k > 0) {
+            pkr_problem pk = *p;
+            pk.precision = stages[k];
             pkr_plan* P2 = nullptr;
-            rc = pkr_plan_create(&p2, stream, &P2);
+            rc = pkr_plan_create(&pk, stream, &P2);
             if (rc == PKR_OK) rc = pkr_plan_load_source(P2, rho, host_buffers);
             if (rc == PKR_OK) rc = pkr_plan_import(P2, P);
-            if (rc == PKR_OK) {
-                pkr_plan_destroy(P);
-                P = P2;
-                const int64_t left = p->max_sweeps - (l32 - 1);
-                rc = left > 0 ? pkr_plan_run(P, left, p->tol, p->tol_kind, p->check_every, &s)
-                              : PKR_OK;
-                upd_bytes += (double)(P->launches - l32) * (double)P->V *
-                             (2.0 * P->lat.Q * 8 + 8);
-            } else if (P2) {
-                pkr_plan_destroy(P2);
+            if (rc != PKR_OK) {
+                if (P2) pkr_plan_destroy(P2);
+                break;
             }
+            pkr_plan_destroy(P);
+            P = P2;
         }
-        launches_total = P->launches;
-    } else {
-        rc = pkr_plan_run(P, p->max_sweeps, p->tol, p->tol_kind, p->check_every, &s);
-        launches_total = P->launches;
-        upd_bytes = (double)launches_total * (double)P->V * (2.0 * P->lat.Q * P->elem + P->elem);
+        const bool last = (k == nst - 1);
+        double t = switch_tol[k];
+        if (!last && p->tol > t) t = p->tol;
+        if (p->tol <= 0.0) t = 0.0;
+        const int64_t left = p->max_sweeps - (P->launches - 1);
+        if (left > 0) rc = pkr_plan_run(P, left, t, p->tol_kind, p->check_every, &s);
+        upd_bytes += (double)(P->launches - prev_launches) * (double)P->V *
+                     (2.0 * P->lat.Q * P->elem + source_bytes(P->prob.precision));
+        prev_launches = P->launches;
+        if (rc != PKR_OK) break;
+        if (p->tol <= 0.0) break;    // fixed step count: first stage only
+        if (s.residual >= 0.0 && s.residual < p->tol) break;
     }
+    const int64_t launches_total = P->launches;
     if (rc == PKR_OK && p->tol > 0.0 && !(s.residual >= 0.0 && s.residual < p->tol))
         rc = PKR_ENOCONV;
     if (rc == PKR_OK || rc == PKR_ENOCONV) {

@@ -38,6 +38,9 @@ struct Coefs {
 enum SweepMode { kPlain = 0, kWritePhi = 1, kCheck = 2 };
 enum SweepVariant { kStaged = 0 };
 
+// Storage precision code of binary16 populations (include/pkr.h: PKR_FP16).
+constexpr int kFP16 = 3;
+
 // One grid of a batch (device-resident descriptor, see pkr_batch.cpp).
 template <typename R>
 struct BatchGrid {
@@ -75,8 +78,14 @@ struct SweepArgs {
     int32_t mode;         // SweepMode
     int32_t zero_in;      // populations in are all zero (first step)
     int32_t small;        // some edge shorter than the lattice reach
-    int32_t pad;
+    int32_t cur;          // index (0/1) of the population array read (binary16 scales)
     double soff;          // constant added to S in this step (mass correction)
+    // binary16 storage only: per-array scales sc[2] (a value v is stored as
+    // v / sc[k]), the running max |p| of this step (float bits) and an
+    // overflow flag
+    float* sc;
+    unsigned int* pmax;
+    int* oflow;
 };
 
 
@@ -100,6 +109,11 @@ int launch_convert(const void* in, int in_precision, void* out, int out_precisio
 // out[i*V + x] = in[i*V + x] - shift[i] (storage conversion with a per-plane
 // shift; shift: Q doubles in device memory).
 int launch_convert_shift(const void* in, int in_precision, void* out, int out_precision, int Q,
-                         int64_t V, const double* shift, void* stream);
+                         int64_t V, const double* shift, void* stream, const float* in_scale = nullptr);
+// binary16 storage: after a step, set the scale of the array the next step
+// writes (sc[next]) from this step's max |p| (4x headroom), reset the max.
+int launch_h16_rescale(float* sc, unsigned int* pmax, int next, void* stream);
+// max |S| of a binary32 source as float bits (atomicMax into *out).
+int launch_absmax_f32(const float* S, int64_t V, unsigned int* out, void* stream);
 
 }  // namespace pkr

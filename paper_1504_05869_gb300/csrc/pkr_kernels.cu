@@ -9,6 +9,8 @@
 
 #include <cstddef>
 
+#include <cuda_fp16.h>
+
 #include "pkr_internal.h"
 
 namespace pkr {
@@ -174,15 +176,45 @@ batch_reduce_kernel(const BatchState* st, int stride_bytes)
 
 __global__ void batch_step_increment_kernel(BatchState* st) { st->step += 1; }
 
-// Storage conversion with a per-plane shift: out[i*V + x] = in[i*V + x] - sh[i].
+// Storage conversion with a per-plane shift: out[i*V + x] = in[i*V + x] - sh[i]
+// (binary16 input: scaled by *scale first).
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(float v) { return (double)v; }
+__device__ __forceinline__ double to_double(__half v) { return (double)__half2float(v); }
+
 template <typename TI, typename TO>
 __global__ void convert_shift_kernel(const TI* __restrict__ in, TO* __restrict__ out, int Q,
-                                     int64_t V, const double* __restrict__ sh)
+                                     int64_t V, const double* __restrict__ sh,
+                                     const float* __restrict__ scale)
 {
     const int64_t n = (int64_t)Q * V;
+    const double sc = scale ? (double)*scale : 1.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
-        out[k] = (TO)((double)in[k] - sh[k / V]);
+        out[k] = (TO)(to_double(in[k]) * sc - sh[k / V]);
+}
+
+__global__ void h16_rescale_kernel(float* sc, unsigned int* pmax, int next)
+{
+    const float m = __uint_as_float(*pmax);
+    if (m > 0.f && isfinite(m)) {
+        // smallest power of two s with 4 m / s <= 65504
+        int e = 0;
+        frexpf(4.0f * m / 65504.0f, &e);
+        sc[next] = ldexpf(1.0f, e);
+    }
+    *pmax = 0u;
+}
+
+__global__ void absmax_f32_kernel(const float* __restrict__ S, int64_t V, unsigned int* out)
+{
+    float m = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += stride)
+        m = fmaxf(m, fabsf(S[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
 // Population storage conversion (binary32 -> binary64 or back), n elements.
@@ -229,24 +261,43 @@ int launch_convert(const void* in, int in_precision, void* out, int out_precisio
 }
 
 int launch_convert_shift(const void* in, int in_precision, void* out, int out_precision, int Q,
-                         int64_t V, const double* shift, void* stream)
+                         int64_t V, const double* shift, void* stream, const float* in_scale)
 {
     const int blocks = 152 * 16;
     cudaStream_t st = (cudaStream_t)stream;
-    if (in_precision == PKR_FP32 && out_precision == PKR_FP64)
-        convert_shift_kernel<float, double><<<blocks, 256, 0, st>>>(
-            static_cast<const float*>(in), static_cast<double*>(out), Q, V, shift);
-    else if (in_precision == PKR_FP64 && out_precision == PKR_FP64)
-        convert_shift_kernel<double, double><<<blocks, 256, 0, st>>>(
-            static_cast<const double*>(in), static_cast<double*>(out), Q, V, shift);
-    else if (in_precision == PKR_FP64 && out_precision == PKR_FP32)
-        convert_shift_kernel<double, float><<<blocks, 256, 0, st>>>(
-            static_cast<const double*>(in), static_cast<float*>(out), Q, V, shift);
-    else if (in_precision == PKR_FP32 && out_precision == PKR_FP32)
-        convert_shift_kernel<float, float><<<blocks, 256, 0, st>>>(
-            static_cast<const float*>(in), static_cast<float*>(out), Q, V, shift);
-    else
+    const float* sc = in_precision == kFP16 ? in_scale : nullptr;
+    if (in_precision == kFP16 && !sc) return (int)cudaErrorInvalidValue;
+#define PKR_CONV(TI, TO)                                                                     \
+    convert_shift_kernel<TI, TO><<<blocks, 256, 0, st>>>(static_cast<const TI*>(in),         \
+                                                         static_cast<TO*>(out), Q, V, shift, sc)
+    if (out_precision == PKR_FP64) {
+        if (in_precision == PKR_FP64) PKR_CONV(double, double);
+        else if (in_precision == PKR_FP32) PKR_CONV(float, double);
+        else if (in_precision == kFP16) PKR_CONV(__half, double);
+        else return (int)cudaErrorInvalidValue;
+    } else if (out_precision == PKR_FP32) {
+        if (in_precision == PKR_FP64) PKR_CONV(double, float);
+        else if (in_precision == PKR_FP32) PKR_CONV(float, float);
+        else if (in_precision == kFP16) PKR_CONV(__half, float);
+        else return (int)cudaErrorInvalidValue;
+    } else {
         return (int)cudaErrorInvalidValue;
+    }
+#undef PKR_CONV
+    return (int)cudaGetLastError();
+}
+
+int launch_h16_rescale(float* sc, unsigned int* pmax, int next, void* stream)
+{
+    h16_rescale_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(sc, pmax, next);
+    return (int)cudaGetLastError();
+}
+
+int launch_absmax_f32(const float* S, int64_t V, unsigned int* out, void* stream)
+{
+    int blocks = (int)((V + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    absmax_f32_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(S, V, out);
     return (int)cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@
 // two integer adds on per-tile wrapped row/column offsets.  Plane i of an
 // array lives at i*V.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -608,6 +609,203 @@ int batch_occupancy_t(int variant, int* blocks)
     return rc;
 }
 
+// ---------------------------------------------------------------------------
+// binary16 storage.  A population value v lives as the binary16 number
+// v / sc[k] in array k, with sc[k] a power of two set before each step so
+// that the step's largest |p| has 4x headroom below 65504; every arithmetic
+// operation is binary32.  cp.async has no 2-byte form, so each lane copies
+// the aligned 4-byte word that holds its value and picks the half by the
+// parity of the element index.  One warp per tile, all Q velocities.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int lds_b32(uint32_t addr)
+{
+    unsigned int v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+template <class L, int TILES>
+__global__ void __launch_bounds__(TILES * 32)
+sweep_h16_kernel(const SweepArgs a, const Coefs<float> c)
+{
+    constexpr int Q = L::Q;
+    constexpr int RC = reach_of<L>();
+    constexpr int W = 2 * RC + 1;
+    constexpr int NC = ncls_of<L>();
+    constexpr int NPB = (Q + 31) / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double rpart[TILES][4];
+    __shared__ float mpart[TILES];
+
+    const int lane = threadIdx.x & 31;
+    const int sub = threadIdx.x >> 5;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem_raw) +
+                           (uint32_t)((sub * Q * 32 + lane) * 4);
+    const __half* __restrict__ A = static_cast<const __half*>(a.A);
+    __half* __restrict__ B = static_cast<__half*>(a.B);
+    const float* __restrict__ S = static_cast<const float*>(a.S);
+    const int64_t V = a.V;
+    const int nxy = a.nx * a.ny;
+    const float sr = a.sc[a.cur];
+    const float inv_sw = 1.0f / a.sc[a.cur ^ 1];
+    const int vodd = (int)(V & 1);
+
+    double rd2 = 0.0, rn2 = 0.0, rmx = 0.0, rms = 0.0;
+    float pmax = 0.f;
+    int of = 0;
+    const int nt = gridDim.x * TILES;
+    for (int tile = blockIdx.x * TILES + sub; tile < a.ntiles; tile += nt) {
+        const int64_t s64 = (int64_t)tile * 32 + lane;
+        const bool valid = s64 < V;
+        const int s = valid ? (int)s64 : 0;
+        const int x = s % a.nx;
+        const int r = s / a.nx;
+        const int y = r % a.ny;
+        const int z = r / a.ny;
+        int xs[W], yo[W], zo[W];
+#pragma unroll
+        for (int d = -RC; d <= RC; ++d) {
+            if (a.small) {
+                xs[d + RC] = wrap_any(x - d, a.nx);
+                yo[d + RC] = wrap_any(y - d, a.ny) * a.nx;
+                zo[d + RC] = wrap_any(z - d, a.nz) * nxy;
+            } else {
+                xs[d + RC] = wrap_near(x - d, a.nx);
+                yo[d + RC] = wrap_near(y - d, a.ny) * a.nx;
+                zo[d + RC] = wrap_near(z - d, a.nz) * nxy;
+            }
+        }
+        const int nbytes = (valid && !a.zero_in) ? 4 : 0;
+        unsigned int pb[NPB];
+#pragma unroll
+        for (int k = 0; k < NPB; ++k) pb[k] = 0u;
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int ox = vx_of<L>(i) + RC;
+            constexpr int oy = vy_of<L>(i) + RC;
+            constexpr int oz = vz_of<L>(i) + RC;
+            const int off = zo[oz] + yo[oy] + xs[ox];
+            const int par = (off ^ ((i & 1) & vodd)) & 1;     // parity of i*V + off
+            const __half* src = A + ((int64_t)i * V + off - par);
+            cp_async<4>(sbase + (uint32_t)(i * 128), src, nbytes);
+            pb[i / 32] |= (unsigned int)par << (i % 32);
+        });
+        cp_async_wait_all();
+
+        // pick each lane's half and rewrite the slot as the scaled binary32
+        // value, so the passes below are those of binary32 storage
+#pragma unroll
+        for (int w = 0; w < NPB; ++w) {
+            const unsigned int bits = pb[w];
+            const int nb = (Q - 32 * w) < 32 ? (Q - 32 * w) : 32;
+#pragma unroll 4
+            for (int b = 0; b < nb; ++b) {
+                const uint32_t ad = sbase + (uint32_t)((32 * w + b) * 128);
+                const unsigned int wd = lds_b32(ad);
+                const unsigned int h = ((bits >> b) & 1u) ? (wd >> 16) : (wd & 0xffffu);
+                const float v = __half2float(__ushort_as_half((unsigned short)h)) * sr;
+                asm volatile("st.shared.f32 [%0], %1;" ::"r"(ad), "f"(v) : "memory");
+            }
+        }
+        const float Phi = density_fixed_f32<Q>(sbase);
+        const float Sx = valid ? (float)((double)S[s] + a.soff) : 0.f;
+        if (valid) {
+            static_for<0, NC>([&](auto CI) {
+                constexpr int cl = decltype(CI)::value;
+                constexpr int i0 = cls_begin<L>(cl), i1 = cls_begin<L>(cl + 1);
+                const float e = fmaf(c.wphi[cl], Phi, c.chi[cl] * Sx);
+                unsigned short* dst = reinterpret_cast<unsigned short*>(B) + ((int64_t)i0 * V + s);
+#pragma unroll 4
+                for (int i = i0; i < i1; ++i) {
+                    const float p = fmaf(c.om1, lds_f32(sbase + (uint32_t)(i * 128)), e);
+                    pmax = fmaxf(pmax, fabsf(p));
+                    float q = p * inv_sw;
+                    if (fabsf(q) > 65504.f) {
+                        of = 1;
+                        q = copysignf(65504.f, q);
+                    }
+                    __stcs(dst, __half_as_ushort(__float2half_rn(q)));
+                    dst += V;
+                }
+            });
+        }
+        if (a.mode != kPlain && valid) {
+            const double ph = (double)Phi;
+            if (a.mode == kCheck) {
+                const double d = ph - a.Phi[s];
+                rd2 += d * d;
+                rn2 += ph * ph;
+                rmx = fmax(rmx, fabs(d));
+                rms += ph;
+            }
+            a.Phi[s] = ph;
+        }
+        __syncwarp();
+    }
+
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_down_sync(0xffffffffu, pmax, o));
+    if (lane == 0) mpart[sub] = pmax;
+    if (a.mode == kCheck) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rd2 += __shfl_down_sync(0xffffffffu, rd2, o);
+            rn2 += __shfl_down_sync(0xffffffffu, rn2, o);
+            rmx = fmax(rmx, __shfl_down_sync(0xffffffffu, rmx, o));
+            rms += __shfl_down_sync(0xffffffffu, rms, o);
+        }
+        if (lane == 0) {
+            rpart[sub][0] = rd2;
+            rpart[sub][1] = rn2;
+            rpart[sub][2] = rmx;
+            rpart[sub][3] = rms;
+        }
+    }
+    if (__any_sync(0xffffffffu, of) && lane == 0) atomicOr(a.oflow, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int k = 0; k < TILES; ++k) m = fmaxf(m, mpart[k]);
+        atomicMax(a.pmax, __float_as_uint(m));
+        if (a.mode == kCheck) {
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+            for (int k = 0; k < TILES; ++k) {
+                t0 += rpart[k][0];
+                t1 += rpart[k][1];
+                t2 = fmax(t2, rpart[k][2]);
+                t3 += rpart[k][3];
+            }
+            a.partials[4 * blockIdx.x + 0] = t0;
+            a.partials[4 * blockIdx.x + 1] = t1;
+            a.partials[4 * blockIdx.x + 2] = t2;
+            a.partials[4 * blockIdx.x + 3] = t3;
+        }
+    }
+}
+
+template <class L>
+int launch_sweep_h16(const SweepArgs& a, const void* coefs, int grid, void* stream)
+{
+    constexpr int TILES = 2;
+    const size_t smem = (size_t)TILES * L::Q * 32 * 4;
+    sweep_h16_kernel<L, TILES><<<grid, TILES * 32, smem, (cudaStream_t)stream>>>(
+        a, *static_cast<const Coefs<float>*>(coefs));
+    return (int)cudaGetLastError();
+}
+
+template <class L>
+int occupancy_h16(int* blocks, int* tiles_per_block)
+{
+    constexpr int TILES = 2;
+    const size_t smem = (size_t)TILES * L::Q * 32 * 4;
+    auto kern = sweep_h16_kernel<L, TILES>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    *tiles_per_block = TILES;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, TILES * 32, smem);
+}
+
 template <class L, typename T, int K>
 int launch_variant(const SweepArgs& a, const void* coefs, int grid, void* stream)
 {
@@ -666,6 +864,8 @@ int variant_count_t() { return Variants<L>::N; }
     template int occupancy_t<L, double>(int, int*, int*);                                    \
     template int occupancy_t<L, float>(int, int*, int*);                                     \
     template int variant_count_t<L>();                                                      \
+    template int launch_sweep_h16<L>(const SweepArgs&, const void*, int, void*);             \
+    template int occupancy_h16<L>(int*, int*);                                               \
     template int launch_batch_t<L, double>(int, BatchState*, int, int, void*);               \
     template int launch_batch_t<L, float>(int, BatchState*, int, int, void*);                \
     template int batch_occupancy_t<L, double>(int, int*);                                    \

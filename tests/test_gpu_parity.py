@@ -337,3 +337,32 @@ def test_fp32_mass_drift_is_removed(pk):
     got = out.cpu().numpy()
     assert abs(got.mean()) < 1e-7 * np.sqrt((got ** 2).mean())
     assert _rel(got, star) < 2e-6
+
+
+@pytest.mark.parametrize("lattice,order,shape,tau", [
+    ("D3Q111", 5, (9, 7, 13), 1.3),
+    ("D3Q111", 5, (16, 16, 16), 15.0),
+    ("D2Q169", 7, (21, 19), 1.5),
+    ("D3Q19", 1, (7, 9, 11), 0.8),
+])
+def test_fixed_steps_fp16(pk, lattice, order, shape, tau):
+    """binary16 storage with per-array power-of-two scales: each stored value
+    is rounded to 2^-11 relative, so after 50 steps Phi stays within 5e-3 of
+    the binary64 oracle (the error does not compound beyond the contraction)."""
+    rho = _rand(shape, 18)
+    steps = 50
+    got, rc, st = _gpu_solve(pk, rho, lattice, order, tau, steps=steps, precision="fp16")
+    ref = oracle.solve(rho, lattice, order, tau_lb=tau, max_steps=steps).phi
+    assert rc == 0
+    assert _rel(got, ref) < 5e-3, _rel(got, ref)
+
+
+def test_mixed16_ladder_reaches_binary64_fixed_point(pk):
+    shape = (12, 10, 14)
+    rho, _ = stiff_source(shape, count=6, sigma=1.5, seed=19)
+    star = oracle.solve(rho, "D3Q111", 5, tau_lb=1.3, tol=1e-15, tol_kind=1,
+                        check_every=8, max_steps=400000).phi
+    got, rc, st = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-12, precision="mixed16",
+                             max_sweeps=400000)
+    assert rc == 0 and st["residual"] < 1e-12
+    assert _rel(got, star) < 5e-9
