@@ -536,6 +536,56 @@ def run_precision(args):
     return 0
 
 
+def run_tau1(args):
+    """The paper's setting tau_lb = 1 (D3Q111 N=5): the scalar-stencil path
+    against the population sweep, per step at 256^3 (64 Gaussians) and for a
+    whole solve to relative residual 1e-10 at 64^3 (same source statistics;
+    at tau_lb = 1 the slowest mode needs ~L^2 steps, 67k at 256^3)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+    from paper_1504_05869_gb300.workloads import stiff_source
+    rho = source()
+    r = torch.from_numpy(rho).cuda()
+    r64 = torch.from_numpy(stiff_source((64, 64, 64), count=16, sigma=2.0, seed=0)[0]).cuda()
+    out = {}
+    for label, var in (("stencil", -1), ("population", 2)):
+        stream = torch.cuda.Stream()
+        prob = pk.problem("D3Q111", SHAPE, 5, tau_lb=1.0, max_sweeps=10 ** 6, variant=var)
+        with pk.Plan(prob, stream=stream) as P:
+            P.load_source(r)
+            P.sweeps(3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.sweeps(20)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 20
+        phi = torch.empty_like(r64)
+        prob = pk.problem("D3Q111", r64.shape, 5, tau_lb=1.0, tol=1e-10, tol_kind="rel_l2",
+                          check_every=SWEEPS_PER_STEP, max_sweeps=10 ** 6, variant=var)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            rc, st = pk.solve(r64, phi, prob, stream=stream)
+        torch.cuda.synchronize()
+        out[label] = {"ms_per_step": ms, "glups": r.numel() / ms / 1e6,
+                      "solve_seconds": time.perf_counter() - t0, "sweeps": st["sweeps"],
+                      "status": rc, "phi": phi}
+    d = (torch.linalg.norm(out["stencil"]["phi"] - out["population"]["phi"]) /
+         torch.linalg.norm(out["population"]["phi"])).item()
+    for v in out.values():
+        v.pop("phi")
+    line = {"metric": "tau_lb = 1 solve time, scalar stencil vs population sweep",
+            "workload": "tau1", "value": out["stencil"]["solve_seconds"], "unit": "s",
+            "higher_is_better": False, "runs": out, "rel_l2_between_paths": d,
+            "stencil_bytes_per_site": 24, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -549,7 +599,7 @@ def main():
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16"])
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "batch", "serve", "poisson2d", "precision"])
+                    choices=["sweep", "batch", "serve", "poisson2d", "precision", "tau1"])
     ap.add_argument("--no-512", action="store_true")
     ap.add_argument("--target-tol", type=float, default=1e-10)
     ap.add_argument("--batch-count", type=int, default=256)
@@ -566,6 +616,8 @@ def main():
         return run_poisson2d(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "tau1":
+        return run_tau1(args)
     configure(args)
     if args.impl == "reference":
         return run_reference(args)

@@ -102,7 +102,12 @@ typedef struct pkr_problem {
     int64_t max_sweeps;   /* upper bound on the steps taken (>= 1) */
     int32_t variant;      /* sweep kernel geometry: -1 = library default, 0 .. count-1 =
                              a compiled variant (pkr_variant_count); all variants give
-                             identical results, they differ only in speed */
+                             identical results, they differ only in speed.  With -1, a
+                             binary64 problem at tau_lb == 1 (omega = 1, the paper's
+                             setting) runs as the scalar stencil Phi' = sum_i phi_i
+                             Phi(x - v_i) + sum_i chi_i S(x - v_i): at omega = 1 the
+                             collision forgets the populations, so this is the same
+                             iteration with 24 instead of 2Q*8+8 bytes per site */
 } pkr_problem;
 
 typedef struct pkr_stats {

@@ -21,6 +21,9 @@ template <class L, typename T> int occupancy_t(int, int*, int*);
 template <class L> int variant_count_t();
 template <class L> int launch_sweep_h16(const SweepArgs&, const void*, int, void*);
 template <class L> int occupancy_h16(int*, int*);
+template <class L>
+int launch_stencil(const double*, double*, const double*, const Coefs<double>&, int64_t, int, int,
+                   int, int, int, double*, int, void*);
 }  // namespace pkr
 
 #define PKR_CK(call)                                     \
@@ -139,6 +142,10 @@ struct pkr_plan {
     int* flag;
     double* host;   // pinned: [0] mean, [1..4] residual, [5] import mean, [6] flag (int),
                     // [7] binary16 overflow flag (int)
+    bool stencil;          // omega = 1, binary64: the state is Phi alone (scalar stencil)
+    double* Ps[2];         // stencil mode: Phi ping-pong
+    double* St;            // stencil mode: sum_i chi_i S(x - v_i)
+    Coefs<double> cchi;    // stencil mode: chi_c in the weight slot (builds St)
     float* h16sc;          // binary16 storage: scales of the two arrays
     unsigned int* h16max;  // binary16 storage: max |p| of the current step
     int* h16of;            // binary16 storage: overflow flag
@@ -149,8 +156,47 @@ struct pkr_plan {
 
 namespace {
 
+int launch_stencil_step(pkr_plan* P, const double* in, double* out, const double* add,
+                        const Coefs<double>& c, int check)
+{
+    const int64_t* n = P->prob.n;
+    const int nx = (int)n[0], ny = (int)n[1], nz = (int)n[2];
+    int rc = 0;
+#define PKR_ST(LL) launch_stencil<LL>(in, out, add, c, P->V, nx, ny, nz, P->small, check, \
+                                      P->partials, P->grid, P->stream)
+    switch (P->prob.lattice) {
+    case PKR_D1Q5: rc = PKR_ST(D1Q5); break;
+    case PKR_D1Q9: rc = PKR_ST(D1Q9); break;
+    case PKR_D1Q13: rc = PKR_ST(D1Q13); break;
+    case PKR_D2Q25: rc = PKR_ST(D2Q25); break;
+    case PKR_D2Q81: rc = PKR_ST(D2Q81); break;
+    case PKR_D2Q169: rc = PKR_ST(D2Q169); break;
+    case PKR_D3Q19: rc = PKR_ST(D3Q19); break;
+    case PKR_D3Q111: rc = PKR_ST(D3Q111); break;
+    default: return PKR_EINVAL;
+    }
+#undef PKR_ST
+    return rc == 0 ? PKR_OK : PKR_ECUDA;
+}
+
 int launch_one(pkr_plan* P, int mode, bool zero_in)
 {
+    if (P->stencil) {
+        // Phi^k = stencil(Phi^(k-1)) + St; a zero-in step keeps Phi^0 = 0
+        if (!zero_in) {
+            const int check = (mode == kCheck) ? 1 : 0;
+            int rc = launch_stencil_step(P, P->Ps[P->cur], P->Ps[P->cur ^ 1], P->St, P->c64,
+                                         check);
+            if (rc != PKR_OK) return rc;
+            if (check &&
+                launch_finalize_residual(P->partials, P->grid, P->scal + 1, P->stream) != 0)
+                return PKR_ECUDA;
+            P->cur ^= 1;
+        }
+        P->Phi = P->Ps[P->cur];
+        P->launches += 1;
+        return PKR_OK;
+    }
     SweepArgs a{};
     a.A = P->pop[P->cur];
     a.B = P->pop[P->cur ^ 1];
@@ -357,6 +403,7 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
     pkr_plan* P = new (std::nothrow) pkr_plan();
     if (!P) return PKR_ENOMEM;
     P->prob = *p;
+    P->stencil = (p->precision == PKR_FP64 && omega == 1.0 && p->variant == -1);
     if (P->prob.epsilon == 0.0) P->prob.epsilon = 1.0;
     if (P->prob.check_every <= 0) P->prob.check_every = 32;
     P->lat = li;
@@ -373,11 +420,13 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
     // collision coefficients per symmetry class
     P->c64.om1 = 1.0 - omega;
     P->c32.om1 = (float)(1.0 - omega);
+    P->cchi.om1 = 0.0;
     for (int c = 0; c < li.ncls; ++c) {
         P->c64.wphi[c] = omega * li.cls_phi[c];
         P->c64.chi[c] = li.cls_chi[c];
         P->c32.wphi[c] = (float)(omega * li.cls_phi[c]);
         P->c32.chi[c] = (float)li.cls_chi[c];
+        P->cchi.wphi[c] = li.cls_chi[c];
     }
 
     int dev = 0, nsm = 0;
@@ -396,7 +445,12 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
         delete P;
         return PKR_EINVAL;
     }
-    if (set_variant(P, var) != PKR_OK) {
+    if (P->stencil) {
+        int64_t g = (P->V + 255) / 256;
+        if (g > (int64_t)nsm * 8) g = (int64_t)nsm * 8;
+        P->grid = (int)g;
+        P->variant = 0;
+    } else if (set_variant(P, var) != PKR_OK) {
         delete P;
         return PKR_ECUDA;
     }
@@ -409,18 +463,24 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
         delete P;
         return PKR_ECUDA;
     }
-    if (plan_bytes(p, li, P->V, kMaxGridBlocks) > freeb) {
+    const size_t need = P->stencil ? (size_t)P->V * 8 * 5 + (size_t)4 * kMaxGridBlocks * 8
+                                   : plan_bytes(p, li, P->V, kMaxGridBlocks);
+    if (need > freeb) {
         delete P;
         return PKR_ENOMEM;
     }
     const size_t nscratch = (size_t)4 * kMaxGridBlocks;
-    bool ok = cudaMalloc(&P->pop[0], popb) == cudaSuccess &&
-              cudaMalloc(&P->pop[1], popb) == cudaSuccess &&
+    bool ok = (P->stencil
+                   ? (cudaMalloc((void**)&P->Ps[0], (size_t)P->V * 8) == cudaSuccess &&
+                      cudaMalloc((void**)&P->Ps[1], (size_t)P->V * 8) == cudaSuccess &&
+                      cudaMalloc((void**)&P->St, (size_t)P->V * 8) == cudaSuccess)
+                   : (cudaMalloc(&P->pop[0], popb) == cudaSuccess &&
+                      cudaMalloc(&P->pop[1], popb) == cudaSuccess)) &&
               cudaMalloc(&P->S, (size_t)P->V * source_bytes(p->precision)) == cudaSuccess &&
               cudaMalloc((void**)&P->h16sc, 2 * sizeof(float)) == cudaSuccess &&
               cudaMalloc((void**)&P->h16max, sizeof(unsigned int)) == cudaSuccess &&
               cudaMalloc((void**)&P->h16of, sizeof(int)) == cudaSuccess &&
-              cudaMalloc((void**)&P->Phi, (size_t)P->V * 8) == cudaSuccess &&
+              (P->stencil || cudaMalloc((void**)&P->Phi, (size_t)P->V * 8) == cudaSuccess) &&
               cudaMalloc((void**)&P->partials, nscratch * 8) == cudaSuccess &&
               cudaMalloc((void**)&P->scal, 8 * 8) == cudaSuccess &&
               cudaMalloc((void**)&P->flag, sizeof(int)) == cudaSuccess &&
@@ -430,6 +490,7 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
         pkr_plan_destroy(P);
         return PKR_ENOMEM;
     }
+    if (P->stencil) P->Phi = P->Ps[0];
     *out = P;
     return PKR_OK;
 }
@@ -437,11 +498,14 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
 int pkr_plan_destroy(pkr_plan* P)
 {
     if (!P) return PKR_OK;
-    if (P->stream || P->pop[0]) cudaStreamSynchronize(P->stream);
+    if (P->stream || P->pop[0] || P->Ps[0]) cudaStreamSynchronize(P->stream);
     cudaFree(P->pop[0]);
     cudaFree(P->pop[1]);
+    cudaFree(P->Ps[0]);
+    cudaFree(P->Ps[1]);
+    cudaFree(P->St);
     cudaFree(P->S);
-    cudaFree(P->Phi);
+    if (!P->stencil) cudaFree(P->Phi);
     cudaFree(P->partials);
     cudaFree(P->scal);
     cudaFree(P->flag);
@@ -499,6 +563,15 @@ int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
         PKR_CK(cudaMemcpyAsync(P->h16sc, sc2, sizeof(sc2), cudaMemcpyHostToDevice, P->stream));
         PKR_CK(cudaMemsetAsync(P->h16max, 0, sizeof(unsigned int), P->stream));
     }
+    if (P->stencil) {
+        // St = sum_i chi_i S(x - v_i); Phi^0 = 0 in both buffers
+        int rc0 = launch_stencil_step(P, static_cast<const double*>(P->S), P->St, nullptr,
+                                      P->cchi, 0);
+        if (rc0 != PKR_OK) return rc0;
+        PKR_CK(cudaMemsetAsync(P->Ps[0], 0, (size_t)P->V * 8, P->stream));
+        PKR_CK(cudaMemsetAsync(P->Ps[1], 0, (size_t)P->V * 8, P->stream));
+        P->Phi = P->Ps[0];
+    }
     // Phi^0 = 0; the first step starts from zero populations
     PKR_CK(cudaMemsetAsync(P->Phi, 0, (size_t)P->V * 8, P->stream));
     P->launches = 0;
@@ -517,7 +590,7 @@ int pkr_plan_autotune(pkr_plan* P, int steps_per_variant, int32_t* best_variant,
                       double* best_ms_per_step)
 {
     if (!P || !P->loaded || steps_per_variant < 1) return PKR_EINVAL;
-    const int n = variant_count(P->prob.lattice);
+    const int n = P->stencil ? 1 : variant_count(P->prob.lattice);
     cudaEvent_t e0, e1;
     PKR_CK(cudaEventCreate(&e0));
     PKR_CK(cudaEventCreate(&e1));
@@ -525,7 +598,7 @@ int pkr_plan_autotune(pkr_plan* P, int steps_per_variant, int32_t* best_variant,
     float best_ms = 1e30f;
     int rc = PKR_OK;
     for (int v = 0; v < n && rc == PKR_OK; ++v) {
-        if ((rc = set_variant(P, v)) != PKR_OK) break;
+        if (!P->stencil && (rc = set_variant(P, v)) != PKR_OK) break;
         if ((rc = launch_one(P, kPlain, false)) != PKR_OK) break;   // warm-up
         cudaEventRecord(e0, P->stream);
         for (int k = 0; k < steps_per_variant && rc == PKR_OK; ++k)
@@ -543,7 +616,7 @@ int pkr_plan_autotune(pkr_plan* P, int steps_per_variant, int32_t* best_variant,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != PKR_OK) return rc;
-    if ((rc = set_variant(P, best)) != PKR_OK) return rc;
+    if (!P->stencil && (rc = set_variant(P, best)) != PKR_OK) return rc;
     // keep the invariant that the latest Phi is written
     if ((rc = launch_one(P, kWritePhi, false)) != PKR_OK) return rc;
     PKR_CK(cudaStreamSynchronize(P->stream));
@@ -555,6 +628,8 @@ int pkr_plan_autotune(pkr_plan* P, int steps_per_variant, int32_t* best_variant,
 int pkr_plan_import(pkr_plan* P, const pkr_plan* F)
 {
     if (!P || !F || !F->loaded || !P->loaded) return PKR_EINVAL;
+    if (F->stencil) return PKR_EINVAL;   // a stencil plan holds no populations to hand on
+    if (P->stencil && F->omega != 1.0) return PKR_EINVAL;
     if (P->prob.lattice != F->prob.lattice || P->prob.order != F->prob.order ||
         P->prob.n[0] != F->prob.n[0] || P->prob.n[1] != F->prob.n[1] ||
         P->prob.n[2] != F->prob.n[2])
@@ -576,6 +651,19 @@ int pkr_plan_import(pkr_plan* P, const pkr_plan* F)
     for (int i = 0; i < P->lat.Q; ++i) shift[i] = c * P->lat.phi[i];
     PKR_CK(cudaMemcpyAsync(P->partials, shift.data(), shift.size() * 8, cudaMemcpyHostToDevice,
                            P->stream));
+    if (P->stencil) {
+        // omega = 1 on both sides: the state is Phi (populations are phi Phi + chi S)
+        if (F->omega != 1.0) return PKR_EINVAL;
+        if (launch_make_source(P->Phi, P->scal + 5, 1.0, P->V, P->Ps[P->cur], PKR_FP64,
+                               P->stream) != 0)
+            return PKR_ECUDA;
+        PKR_CK(cudaStreamSynchronize(P->stream));
+        P->Phi = P->Ps[P->cur];
+        P->launches = F->launches;
+        P->last_residual = F->last_residual;
+        P->soff_next = 0.0;
+        return PKR_OK;
+    }
     if (P->prob.precision == PKR_FP16) return PKR_EINVAL;   // imports into binary16: no
     if (launch_convert_shift(F->pop[F->cur], F->prob.precision, P->pop[P->cur], P->prob.precision,
                              P->lat.Q, P->V, P->partials, P->stream, F->h16sc + F->cur) != 0 ||
@@ -678,7 +766,7 @@ int pkr_plan_phi(pkr_plan* P, double* phi, int phi_on_host)
 
 int64_t pkr_plan_steps(const pkr_plan* P) { return P && P->launches > 0 ? P->launches - 1 : 0; }
 
-void* pkr_plan_populations(pkr_plan* P) { return P ? P->pop[P->cur] : nullptr; }
+void* pkr_plan_populations(pkr_plan* P) { return (P && !P->stencil) ? P->pop[P->cur] : nullptr; }
 
 int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buffers,
               pkr_stats* st, void* stream)

@@ -806,6 +806,106 @@ int occupancy_h16(int* blocks, int* tiles_per_block)
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, TILES * 32, smem);
 }
 
+// ---------------------------------------------------------------------------
+// omega = 1 (tau_lb = 1, the paper's setting): the collision forgets the
+// pulled populations, f_i = phi_i Phi + chi_i S, so one step is the scalar
+// stencil  Phi'(x) = sum_i w_i Phi(x - v_i) + St(x)  with w_i = phi_i and
+// St = sum_i chi_i S(x - v_i) (the same kernel with w_i = chi_i, St = 0,
+// builds St once).  One thread per site; the Q neighbour reads hit L1/L2.
+// On check steps it adds |dPhi|^2, |Phi|^2, max |dPhi| and sum Phi of its
+// block to partials (4 doubles per block).
+// ---------------------------------------------------------------------------
+template <class L>
+__global__ void __launch_bounds__(256)
+stencil_kernel(const double* __restrict__ Pin, double* __restrict__ Pout,
+               const double* __restrict__ St, const Coefs<double> c, int64_t V, int nx, int ny,
+               int nz, int small, int check, double* partials)
+{
+    constexpr int Q = L::Q;
+    constexpr int RC = reach_of<L>();
+    constexpr int W = 2 * RC + 1;
+    __shared__ double red[8][4];
+    const int nxy = nx * ny;
+    double d2 = 0.0, n2 = 0.0, mx = 0.0, ms = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s64 < V; s64 += stride) {
+        const int s = (int)s64;
+        const int x = s % nx;
+        const int r = s / nx;
+        const int y = r % ny;
+        const int z = r / ny;
+        int xs[W], yo[W], zo[W];
+#pragma unroll
+        for (int d = -RC; d <= RC; ++d) {
+            if (small) {
+                xs[d + RC] = wrap_any(x - d, nx);
+                yo[d + RC] = wrap_any(y - d, ny) * nx;
+                zo[d + RC] = wrap_any(z - d, nz) * nxy;
+            } else {
+                xs[d + RC] = wrap_near(x - d, nx);
+                yo[d + RC] = wrap_near(y - d, ny) * nx;
+                zo[d + RC] = wrap_near(z - d, nz) * nxy;
+            }
+        }
+        double acc = St ? St[s] : 0.0;
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int ox = vx_of<L>(i) + RC;
+            constexpr int oy = vy_of<L>(i) + RC;
+            constexpr int oz = vz_of<L>(i) + RC;
+            acc = fma(c.wphi[cls_of<L>(i)], __ldg(Pin + (zo[oz] + yo[oy] + xs[ox])), acc);
+        });
+        Pout[s] = acc;
+        if (check) {
+            const double d = acc - Pin[s];
+            d2 += d * d;
+            n2 += acc * acc;
+            mx = fmax(mx, fabs(d));
+            ms += acc;
+        }
+    }
+    if (check) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            d2 += __shfl_down_sync(0xffffffffu, d2, o);
+            n2 += __shfl_down_sync(0xffffffffu, n2, o);
+            mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            ms += __shfl_down_sync(0xffffffffu, ms, o);
+        }
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) {
+            red[w][0] = d2;
+            red[w][1] = n2;
+            red[w][2] = mx;
+            red[w][3] = ms;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+            for (int k = 0; k < 8; ++k) {
+                t0 += red[k][0];
+                t1 += red[k][1];
+                t2 = fmax(t2, red[k][2]);
+                t3 += red[k][3];
+            }
+            partials[4 * blockIdx.x + 0] = t0;
+            partials[4 * blockIdx.x + 1] = t1;
+            partials[4 * blockIdx.x + 2] = t2;
+            partials[4 * blockIdx.x + 3] = t3;
+        }
+    }
+}
+
+template <class L>
+int launch_stencil(const double* Pin, double* Pout, const double* St, const Coefs<double>& c,
+                   int64_t V, int nx, int ny, int nz, int small, int check, double* partials,
+                   int grid, void* stream)
+{
+    stencil_kernel<L><<<grid, 256, 0, (cudaStream_t)stream>>>(Pin, Pout, St, c, V, nx, ny, nz,
+                                                              small, check, partials);
+    return (int)cudaGetLastError();
+}
+
 template <class L, typename T, int K>
 int launch_variant(const SweepArgs& a, const void* coefs, int grid, void* stream)
 {
@@ -866,6 +966,8 @@ int variant_count_t() { return Variants<L>::N; }
     template int variant_count_t<L>();                                                      \
     template int launch_sweep_h16<L>(const SweepArgs&, const void*, int, void*);             \
     template int occupancy_h16<L>(int*, int*);                                               \
+    template int launch_stencil<L>(const double*, double*, const double*, const Coefs<double>&,  \
+                                   int64_t, int, int, int, int, int, double*, int, void*);      \
     template int launch_batch_t<L, double>(int, BatchState*, int, int, void*);               \
     template int launch_batch_t<L, float>(int, BatchState*, int, int, void*);                \
     template int batch_occupancy_t<L, double>(int, int*);                                    \

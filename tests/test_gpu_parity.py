@@ -366,3 +366,37 @@ def test_mixed16_ladder_reaches_binary64_fixed_point(pk):
                              max_sweeps=400000)
     assert rc == 0 and st["residual"] < 1e-12
     assert _rel(got, star) < 5e-9
+
+
+@pytest.mark.parametrize("lattice,order,shape", [
+    ("D3Q111", 5, (9, 7, 13)), ("D2Q169", 7, (21, 19)), ("D1Q13", 7, (100,)),
+    ("D3Q19", 1, (7, 9, 11)), ("D3Q111", 5, (2, 3, 5)),
+])
+def test_tau1_scalar_stencil(pk, lattice, order, shape):
+    """At tau_lb = 1 the library runs the scalar stencil (no populations); it
+    matches the oracle's population scheme and the forced population sweep."""
+    rho = _rand(shape, 20)
+    for steps in (1, 2, 17):
+        ref = oracle.solve(rho, lattice, order, tau_lb=1.0, max_steps=steps).phi
+        st_path, rc, st = _gpu_solve(pk, rho, lattice, order, 1.0, steps=steps)
+        import torch
+        prob = pk.problem(lattice, rho.shape, order, tau_lb=1.0, max_sweeps=steps, variant=0)
+        r = torch.from_numpy(rho).cuda()
+        phi = torch.empty_like(r)
+        rc2, _ = pk.solve(r, phi, prob)
+        assert rc == 0 and rc2 == 0 and st["sweeps"] == steps
+        assert _rel(st_path, ref) <= FP64_TOL
+        assert _rel(phi.cpu().numpy(), ref) <= FP64_TOL
+
+
+def test_tau1_converged_and_mixed(pk):
+    shape = (12, 10, 14)
+    rho, _ = stiff_source(shape, count=6, sigma=1.5, seed=21)
+    ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.0, tol=1e-11, tol_kind=1, check_every=8,
+                       max_steps=400000)
+    got, rc, st = _gpu_solve(pk, rho, "D3Q111", 5, 1.0, tol=1e-11, max_sweeps=400000)
+    assert rc == 0 and st["sweeps"] == ref.steps
+    assert _rel(got, ref.phi) <= FP64_TOL
+    mixed, rc2, st2 = _gpu_solve(pk, rho, "D3Q111", 5, 1.0, tol=1e-11, precision="mixed",
+                                 max_sweeps=400000)
+    assert rc2 == 0 and _rel(mixed, ref.phi) < 1e-8
