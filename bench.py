@@ -207,7 +207,7 @@ def run(args):
         plan = pk.Plan(prob, stream=stream)
         plan.load_source(r_dev)
     Q = {"D3Q111": 111, "D3Q19": 19}[LATTICE]
-    esize = 8 if PRECISION == "fp64" else 4
+    esize = {"fp64": 8, "fx64": 8, "fp32": 4, "fp16": 2}[PRECISION]
     tau = None
 
     def step():
@@ -242,7 +242,7 @@ def run(args):
         dist.barrier()
     sweeps = args.steps * SWEEPS_PER_STEP
     glups = world * V * sweeps / (dev_ms * 1e-3) / 1e9
-    bytes_site = 2 * Q * esize + esize
+    bytes_site = 2 * Q * esize + (8 if PRECISION in ("fp64", "fx64") else 4)
     # per-launch: plain sweeps move 2*Q*8 + 8 bytes per site
     launch_ms = dev_ms / sweeps
     achieved = V * bytes_site / (launch_ms * 1e-3) / 1e9
@@ -289,7 +289,8 @@ def run(args):
             "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if PRECISION == "fp64" else "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fx64": "int64 (fixed point)", "fp32": "f32",
+                      "fp16": "f16"}[PRECISION], "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(SHAPE), "lattice": LATTICE,
                        "order": ORDER, "knudsen": KN, "tau_lb": tau,
                        "sweeps_per_step": SWEEPS_PER_STEP, "residual_check": "rel_l2 fp64",
@@ -300,8 +301,8 @@ def run(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak,
                          "traffic": recorded_traffic(), "peak_source": peak_src,
-                         "kernel": f"sweep_kernel<{LATTICE},"
-                                   f"{'double' if PRECISION == 'fp64' else 'float'}>",
+                         "kernel": f"sweep_staged_kernel<{LATTICE},"
+                                   f"{ {'fp64': 'double', 'fx64': 'long long'}.get(PRECISION, 'float') }>",
                          "algorithmic_bytes_per_launch": V * bytes_site},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * (SWEEPS_PER_STEP + 1),
@@ -597,7 +598,7 @@ def main():
     ap.add_argument("--size", type=int, default=0, help="cube edge (default 256)")
     ap.add_argument("--lattice", default="D3Q111", choices=["D3Q111", "D3Q19"])
     ap.add_argument("--order", type=int, default=5)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16", "fx64"])
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "batch", "serve", "poisson2d", "precision", "tau1"])
     ap.add_argument("--no-512", action="store_true")

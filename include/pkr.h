@@ -76,9 +76,18 @@ typedef enum pkr_lattice {
  * (set before each step so that the step's largest value has 4x headroom),
  * arithmetic in binary32, source in binary32; accurate to ~1e-4 of Phi.
  * MIXED16 (pkr_solve only): binary16 to PKR_MIXED16_SWITCH_TOL, binary32 to
- * PKR_MIXED_SWITCH_TOL, then binary64 to tol. */
+ * PKR_MIXED_SWITCH_TOL, then binary64 to tol.
+ * FX64: populations stored as 64-bit integers v 2^F with a power-of-two scale
+ * per array (F lowered on the device whenever the largest stored value
+ * passes 2^54).  The density is an exact integer sum and the relaxation a
+ * 64 x 64-bit fixed-point product by (1 - omega) (rounded to nearest) plus
+ * the per-class equilibrium-and-source term; only that term and the density
+ * conversion use binary64.  Every value keeps >= 54 significant bits relative
+ * to the largest stored value, as accurate as binary64 for the field as a
+ * whole.  On GPUs with little binary64 throughput it runs the sweep on the
+ * integer units. */
 typedef enum pkr_precision {
-    PKR_FP64 = 0, PKR_FP32 = 1, PKR_MIXED = 2, PKR_FP16 = 3, PKR_MIXED16 = 4
+    PKR_FP64 = 0, PKR_FP32 = 1, PKR_MIXED = 2, PKR_FP16 = 3, PKR_MIXED16 = 4, PKR_FX64 = 5
 } pkr_precision;
 #define PKR_MIXED_SWITCH_TOL 1e-6
 #define PKR_MIXED16_SWITCH_TOL 1e-3

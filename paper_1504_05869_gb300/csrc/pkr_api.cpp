@@ -37,14 +37,16 @@ namespace {
 template <class L>
 int dispatch_launch(int var, int prec, const SweepArgs& a, const void* c, int grid, void* st)
 {
-    return prec == PKR_FP64 ? launch_sweep_t<L, double>(var, a, c, grid, st)
-                            : launch_sweep_t<L, float>(var, a, c, grid, st);
+    if (prec == PKR_FP64) return launch_sweep_t<L, double>(var, a, c, grid, st);
+    if (prec == PKR_FX64) return launch_sweep_t<L, long long>(var, a, c, grid, st);
+    return launch_sweep_t<L, float>(var, a, c, grid, st);
 }
 template <class L>
 int dispatch_occ(int var, int prec, int* b, int* tpb)
 {
-    return prec == PKR_FP64 ? occupancy_t<L, double>(var, b, tpb)
-                            : occupancy_t<L, float>(var, b, tpb);
+    if (prec == PKR_FP64) return occupancy_t<L, double>(var, b, tpb);
+    if (prec == PKR_FX64) return occupancy_t<L, long long>(var, b, tpb);
+    return occupancy_t<L, float>(var, b, tpb);
 }
 
 int64_t tiles_of(const int64_t n[3]) { return (n[0] * n[1] * n[2] + 31) / 32; }
@@ -77,11 +79,11 @@ int default_variant(int lattice, int precision)
 
 int elem_bytes(int precision)
 {
-    return precision == PKR_FP64 ? 8 : precision == PKR_FP32 ? 4 : 2;
+    return (precision == PKR_FP64 || precision == PKR_FX64) ? 8 : precision == PKR_FP32 ? 4 : 2;
 }
-// Bytes of one source value: binary64 plans keep S in binary64, the others
-// in binary32.
-int source_bytes(int precision) { return precision == PKR_FP64 ? 8 : 4; }
+// binary64 and fixed-point plans keep S in binary64, the others in binary32.
+bool wide_source(int precision) { return precision == PKR_FP64 || precision == PKR_FX64; }
+int source_bytes(int precision) { return wide_source(precision) ? 8 : 4; }
 
 double now_ms()
 {
@@ -93,7 +95,8 @@ int validate(const pkr_problem* p, LatticeInfo* li, double* tau)
 {
     if (!p) return PKR_EINVAL;
     if (p->dim < 1 || p->dim > 3) return PKR_EINVAL;
-    if (p->precision != PKR_FP64 && p->precision != PKR_FP32 && p->precision != PKR_FP16)
+    if (p->precision != PKR_FP64 && p->precision != PKR_FP32 && p->precision != PKR_FP16 &&
+        p->precision != PKR_FX64)
         return PKR_EINVAL;
     // (PKR_MIXED / PKR_MIXED16 are resolved by pkr_solve into a ladder of plans)
     int rc = build_lattice(p->lattice, p->order, li);
@@ -149,6 +152,9 @@ struct pkr_plan {
     float* h16sc;          // binary16 storage: scales of the two arrays
     unsigned int* h16max;  // binary16 storage: max |p| of the current step
     int* h16of;            // binary16 storage: overflow flag
+    int* fxF;              // fixed-point storage: exponents of the two arrays
+    unsigned long long* fxmax;  // fixed-point storage: max |stored| of the current step
+    long long cfx;         // fixed-point storage: round((1 - omega) 2^62)
     bool loaded;
     Coefs<double> c64;
     Coefs<float> c32;
@@ -213,11 +219,14 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
     a.small = P->small;
     a.soff = P->soff_next;
     P->soff_next = 0.0;
-    const void* c = P->prob.precision == PKR_FP64 ? (const void*)&P->c64 : (const void*)&P->c32;
+    const void* c = wide_source(P->prob.precision) ? (const void*)&P->c64 : (const void*)&P->c32;
     int rc = 0;
     const int pr = P->prob.precision;
     const int vr = P->variant;
     a.cur = P->cur;
+    a.fxF = P->fxF;
+    a.fxmax = P->fxmax;
+    a.cfx = P->cfx;
     a.sc = P->h16sc;
     a.pmax = P->h16max;
     a.oflow = P->h16of;
@@ -255,6 +264,9 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
     default: return PKR_EINVAL;
     }
     if (rc != 0) return PKR_ECUDA;
+    // fixed point: the array this step read is the one the next step writes
+    if (pr == PKR_FX64 && launch_fx_rescale(P->fxF, P->fxmax, P->cur, P->stream) != 0)
+        return PKR_ECUDA;
     P->cur ^= 1;
     P->launches += 1;
     if (mode == kCheck) {
@@ -421,6 +433,7 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
     P->c64.om1 = 1.0 - omega;
     P->c32.om1 = (float)(1.0 - omega);
     P->cchi.om1 = 0.0;
+    P->cfx = std::llround(std::ldexp(1.0 - omega, 62));
     for (int c = 0; c < li.ncls; ++c) {
         P->c64.wphi[c] = omega * li.cls_phi[c];
         P->c64.chi[c] = li.cls_chi[c];
@@ -480,6 +493,8 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
               cudaMalloc((void**)&P->h16sc, 2 * sizeof(float)) == cudaSuccess &&
               cudaMalloc((void**)&P->h16max, sizeof(unsigned int)) == cudaSuccess &&
               cudaMalloc((void**)&P->h16of, sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void**)&P->fxF, 2 * sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void**)&P->fxmax, sizeof(unsigned long long)) == cudaSuccess &&
               (P->stencil || cudaMalloc((void**)&P->Phi, (size_t)P->V * 8) == cudaSuccess) &&
               cudaMalloc((void**)&P->partials, nscratch * 8) == cudaSuccess &&
               cudaMalloc((void**)&P->scal, 8 * 8) == cudaSuccess &&
@@ -512,6 +527,8 @@ int pkr_plan_destroy(pkr_plan* P)
     cudaFree(P->h16sc);
     cudaFree(P->h16max);
     cudaFree(P->h16of);
+    cudaFree(P->fxF);
+    cudaFree(P->fxmax);
     if (P->host) cudaFreeHost(P->host);
     delete P;
     return PKR_OK;
@@ -530,8 +547,13 @@ int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
     if (launch_rho_partials(rd, P->V, P->partials, P->red_blocks, P->flag, P->stream) != 0 ||
         launch_finalize_mean(P->partials, P->red_blocks, P->V, P->scal, P->stream) != 0 ||
         launch_make_source(rd, P->scal, P->scale, P->V, P->S,
-                           P->prob.precision == PKR_FP64 ? PKR_FP64 : PKR_FP32, P->stream) != 0)
+                           wide_source(P->prob.precision) ? PKR_FP64 : PKR_FP32, P->stream) != 0)
         return PKR_ECUDA;
+    if (P->prob.precision == PKR_FX64) {
+        PKR_CK(cudaMemsetAsync(P->fxmax, 0, sizeof(unsigned long long), P->stream));
+        if (launch_absmax_f64(static_cast<const double*>(P->S), P->V, P->fxmax, P->stream) != 0)
+            return PKR_ECUDA;
+    }
     if (P->prob.precision == PKR_FP16) {
         PKR_CK(cudaMemsetAsync(P->h16max, 0, sizeof(unsigned int), P->stream));
         PKR_CK(cudaMemsetAsync(P->h16of, 0, sizeof(int), P->stream));
@@ -548,6 +570,23 @@ int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
         return PKR_EINVAL;
     }
     P->rho_mean = P->host[0];
+    if (P->prob.precision == PKR_FX64) {
+        // exponent of the first write (the step from zero stores chi_i S):
+        // its largest value lands near 2^52, leaving room to grow before the
+        // device-side rescaling shifts the scale
+        unsigned long long mb = 0;
+        PKR_CK(cudaMemcpy(&mb, P->fxmax, sizeof(mb), cudaMemcpyDeviceToHost));
+        double ms = 0.0;
+        std::memcpy(&ms, &mb, sizeof(ms));
+        double mchi = 0.0;
+        for (int i = 0; i < P->lat.Q; ++i) mchi = std::fmax(mchi, std::fabs(P->lat.chi[i]));
+        const double m = ms * mchi;
+        int F = 0;
+        if (m > 0.0 && std::isfinite(m)) F = 52 - (std::ilogb(m) + 1);
+        const int F2[2] = {F, F};
+        PKR_CK(cudaMemcpyAsync(P->fxF, F2, sizeof(F2), cudaMemcpyHostToDevice, P->stream));
+        PKR_CK(cudaMemsetAsync(P->fxmax, 0, sizeof(unsigned long long), P->stream));
+    }
     if (P->prob.precision == PKR_FP16) {
         // scale of the first write: the step from zero stores chi_i S
         unsigned int mb = 0;
@@ -664,7 +703,9 @@ int pkr_plan_import(pkr_plan* P, const pkr_plan* F)
         P->soff_next = 0.0;
         return PKR_OK;
     }
-    if (P->prob.precision == PKR_FP16) return PKR_EINVAL;   // imports into binary16: no
+    if (P->prob.precision == PKR_FP16 || P->prob.precision == PKR_FX64 ||
+        F->prob.precision == PKR_FX64)
+        return PKR_EINVAL;   // imports into binary16 or fixed point, or from fixed point: no
     if (launch_convert_shift(F->pop[F->cur], F->prob.precision, P->pop[P->cur], P->prob.precision,
                              P->lat.Q, P->V, P->partials, P->stream, F->h16sc + F->cur) != 0 ||
         launch_make_source(P->Phi, P->scal + 5, 1.0, P->V, P->Phi, PKR_FP64, P->stream) != 0)
@@ -716,7 +757,8 @@ int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check
             // exact value 0 (the source has zero mean).  Remove it in the next
             // step through the source: sum_i chi_i = 1, so adding -M/V to S at
             // every site removes exactly M.
-            if (P->prob.precision != PKR_FP64 && std::isfinite(P->host[4]))
+            if ((P->prob.precision == PKR_FP32 || P->prob.precision == PKR_FP16) &&
+                std::isfinite(P->host[4]))
                 P->soff_next = -P->host[4] / (double)P->V;
             if (P->prob.precision == PKR_FP16) {
                 int of = 0;

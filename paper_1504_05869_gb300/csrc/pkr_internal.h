@@ -40,6 +40,8 @@ enum SweepVariant { kStaged = 0 };
 
 // Storage precision code of binary16 populations (include/pkr.h: PKR_FP16).
 constexpr int kFP16 = 3;
+// Storage precision code of 64-bit fixed-point populations (PKR_FX64).
+constexpr int kFX64 = 5;
 
 // One grid of a batch (device-resident descriptor, see pkr_batch.cpp).
 template <typename R>
@@ -86,6 +88,12 @@ struct SweepArgs {
     float* sc;
     unsigned int* pmax;
     int* oflow;
+    // 64-bit fixed-point storage only: exponents fxF[2] (a value v is stored
+    // as round(v 2^fxF[k]) in array k), max |stored| of this step, and
+    // 1 - omega as round((1 - omega) 2^62)
+    int* fxF;
+    unsigned long long* fxmax;
+    long long cfx;
 };
 
 
@@ -113,6 +121,11 @@ int launch_convert_shift(const void* in, int in_precision, void* out, int out_pr
 // binary16 storage: after a step, set the scale of the array the next step
 // writes (sc[next]) from this step's max |p| (4x headroom), reset the max.
 int launch_h16_rescale(float* sc, unsigned int* pmax, int next, void* stream);
+// 64-bit fixed-point storage: after a step, set the exponent of the array the
+// next step writes from this step's max |stored| (keep it below 2^54), reset.
+int launch_fx_rescale(int* F, unsigned long long* fmax, int next, void* stream);
+// max |S| of a binary64 source as bits (atomicMax into *out).
+int launch_absmax_f64(const double* S, int64_t V, unsigned long long* out, void* stream);
 // max |S| of a binary32 source as float bits (atomicMax into *out).
 int launch_absmax_f32(const float* S, int64_t V, unsigned int* out, void* stream);
 

@@ -206,6 +206,28 @@ __global__ void h16_rescale_kernel(float* sc, unsigned int* pmax, int next)
     *pmax = 0u;
 }
 
+__global__ void fx_rescale_kernel(int* F, unsigned long long* fmax, int next)
+{
+    const unsigned long long m = *fmax;
+    int sh = 0;
+    if (m > (1ull << 54)) sh = (64 - __clzll((long long)m)) - 52;
+    F[next] = F[next ^ 1] - sh;
+    *fmax = 0ull;
+}
+
+__global__ void absmax_f64_kernel(const double* __restrict__ S, int64_t V,
+                                  unsigned long long* out)
+{
+    double m = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += stride)
+        m = fmax(m, fabs(S[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 __global__ void absmax_f32_kernel(const float* __restrict__ S, int64_t V, unsigned int* out)
 {
     float m = 0.f;
@@ -290,6 +312,20 @@ int launch_convert_shift(const void* in, int in_precision, void* out, int out_pr
 int launch_h16_rescale(float* sc, unsigned int* pmax, int next, void* stream)
 {
     h16_rescale_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(sc, pmax, next);
+    return (int)cudaGetLastError();
+}
+
+int launch_fx_rescale(int* F, unsigned long long* fmax, int next, void* stream)
+{
+    fx_rescale_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(F, fmax, next);
+    return (int)cudaGetLastError();
+}
+
+int launch_absmax_f64(const double* S, int64_t V, unsigned long long* out, void* stream)
+{
+    int blocks = (int)((V + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    absmax_f64_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(S, V, out);
     return (int)cudaGetLastError();
 }
 

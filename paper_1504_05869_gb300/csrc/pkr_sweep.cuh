@@ -55,6 +55,10 @@ __host__ __device__ __forceinline__ void static_for(F&& f)
 }
 
 template <typename T> struct AccType { using type = T; };
+template <> struct AccType<long long> { using type = double; };
+// Type of the stored source: binary64 for fixed-point populations.
+template <typename T> struct SrcType { using type = T; };
+template <> struct SrcType<long long> { using type = double; };
 
 __device__ __forceinline__ int wrap_near(int c, int n)
 {
@@ -69,6 +73,7 @@ __device__ __forceinline__ int wrap_any(int c, int n)
 
 __device__ __forceinline__ void store_stream(double* p, double v) { __stcs(p, v); }
 __device__ __forceinline__ void store_stream(float* p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void store_stream(long long* p, long long v) { __stcs(p, v); }
 
 // ---------------------------------------------------------------------------
 // Staged sweep: one warp owns a tile of 32 consecutive sites and all Q
@@ -253,18 +258,47 @@ __device__ __forceinline__ float density_fixed_f32(uint32_t col)   // stride 128
 template <typename T> __device__ __forceinline__ T lds_val(uint32_t addr);
 template <> __device__ __forceinline__ double lds_val<double>(uint32_t addr) { return lds_f64(addr); }
 template <> __device__ __forceinline__ float lds_val<float>(uint32_t addr) { return lds_f32(addr); }
+template <> __device__ __forceinline__ long long lds_val<long long>(uint32_t addr)
+{
+    long long v;
+    asm volatile("ld.shared.s64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
 
 // One grid as a tile step sees it.
 template <typename T>
 struct TileGrid {
     const T* A;     // populations in (pulled)
     T* B;           // populations out
-    const T* S;     // source
+    const typename SrcType<T>::type* S;   // source
     double* Phi;    // density (written on write/check sweeps)
     int64_t V;
     int nx, ny, nz, small;
     double soff;    // constant added to S in this step (mass correction)
+    int fr, fw;     // fixed-point storage: exponents of the read and written arrays
+    long long cfx;  // fixed-point storage: round((1 - omega) 2^62)
 };
+
+__device__ __forceinline__ long long lds_s64(uint32_t addr)
+{
+    long long v;
+    asm volatile("ld.shared.s64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+
+// round(q c / 2^(62 + sh)) for the fixed-point relaxation (c = (1 - omega) 2^62)
+__device__ __forceinline__ long long fx_mul(long long q, long long c, int sh)
+{
+    const int s = 62 + sh;
+    const __int128 prod = (__int128)q * (__int128)c + ((__int128)1 << (s - 1));
+    return (long long)(prod >> s);
+}
+
+// 2^e as a binary64 (|e| < 1000)
+__device__ __forceinline__ double pow2(int e)
+{
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
 
 // One 32-site tile of one grid, executed by the G warps of a tile slot:
 // pull (cp.async), density, relax + store, density output.  On check sweeps
@@ -276,7 +310,7 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
                                           int mode, bool zero_in, int lane, int grp, int sub,
                                           uint32_t sbase, long long (&xacc)[TILES][G][32],
                                           int (&xexp)[TILES][G][32], double& d2, double& n2,
-                                          double& mx, double& ms)
+                                          double& mx, double& ms, unsigned long long& fxm)
 {
     using R = typename AccType<T>::type;
     using ST = Staged<L, T, G, TILES>;
@@ -334,7 +368,20 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
         // density (the G warps of a tile meet twice at named barrier 1 + sub;
         // both barriers sit outside every lane-dependent branch)
         R Phi;
-        if constexpr (std::is_same<T, double>::value) {
+        if constexpr (std::is_same<T, long long>::value) {
+            // fixed point: the density is an exact integer sum
+            long long part = 0;
+#pragma unroll 8
+            for (int k = 0; k < n; ++k) part += lds_s64(sbase + k * 256);
+            if constexpr (G > 1) {
+                xacc[sub][g][lane] = part;
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+                part = 0;
+#pragma unroll
+                for (int k = 0; k < G; ++k) part += xacc[sub][k][lane];
+            }
+            Phi = (double)part * pow2(-tg.fr);
+        } else if constexpr (std::is_same<T, double>::value) {
             int emax = max_exponent<n>(sbase);
             if constexpr (G > 1) {
                 xexp[sub][g][lane] = emax;
@@ -393,7 +440,20 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
                 constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
                 constexpr int i0 = cb > lo ? cb : lo;
                 constexpr int i1 = ce < hi ? ce : hi;
-                if constexpr (i0 < i1) {
+                if constexpr (i0 < i1 && std::is_same<T, long long>::value) {
+                    const double e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
+                    const long long ei = __double2ll_rn(e * pow2(tg.fw));
+                    const int sh = tg.fr - tg.fw;
+                    T* dst = B + ((int64_t)i0 * V + s);
+#pragma unroll 4
+                    for (int i = i0; i < i1; ++i) {
+                        const long long p = fx_mul(lds_s64(sbase + (i - lo) * 256), tg.cfx, sh) + ei;
+                        const unsigned long long ap = (unsigned long long)(p < 0 ? -p : p);
+                        fxm = ap > fxm ? ap : fxm;
+                        store_stream(dst, (T)p);
+                        dst += V;
+                    }
+                } else if constexpr (i0 < i1) {
                     const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
                     T* dst = B + ((int64_t)i0 * V + s);
                     int i = i0;
@@ -450,15 +510,26 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     const int sub = wib / G;     // tile slot of this warp in the block
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(
         reinterpret_cast<T*>(smem_raw) + (size_t)wib * ST::CH * 32 + lane);
+    const bool fx = std::is_same<T, long long>::value;
     const TileGrid<T> tg{static_cast<const T*>(a.A), static_cast<T*>(a.B),
-                         static_cast<const T*>(a.S), a.Phi, a.V, a.nx, a.ny, a.nz, a.small,
-                         a.soff};
+                         static_cast<const typename SrcType<T>::type*>(a.S), a.Phi, a.V, a.nx,
+                         a.ny, a.nz, a.small, a.soff, fx ? a.fxF[a.cur] : 0,
+                         fx ? a.fxF[a.cur ^ 1] : 0, a.cfx};
 
     double rd2 = 0.0, rn2 = 0.0, rmx = 0.0, rms = 0.0;
+    unsigned long long fxm = 0ull;
     const int nt = gridDim.x * TILES;
     for (int tile = blockIdx.x * TILES + sub; tile < a.ntiles; tile += nt)
         tile_step<L, T, G, TILES>(tg, c, tile, a.mode, a.zero_in != 0, lane, grp, sub, sbase,
-                                  xacc, xexp, rd2, rn2, rmx, rms);
+                                  xacc, xexp, rd2, rn2, rmx, rms, fxm);
+    if constexpr (std::is_same<T, long long>::value) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_down_sync(0xffffffffu, fxm, o);
+            fxm = v > fxm ? v : fxm;
+        }
+        if (lane == 0 && fxm) atomicMax(a.fxmax, fxm);
+    }
 
     if (a.mode == kCheck) {
         if (grp == 0) {
@@ -543,11 +614,12 @@ sweep_batch_kernel(BatchState* st, int K)
         if (age >= 1 && (age + 1) % K == 0) mode = kCheck;
         else if (zero_in || (age + 2) % K == 0) mode = kWritePhi;
         const TileGrid<T> tg{static_cast<const T*>(gd.pop[cur]), static_cast<T*>(gd.pop[cur ^ 1]),
-                             static_cast<const T*>(gd.S), gd.Phi, gd.V, gd.nx, gd.ny, gd.nz,
-                             gd.small, 0.0};
+                             static_cast<const typename SrcType<T>::type*>(gd.S), gd.Phi, gd.V,
+                             gd.nx, gd.ny, gd.nz, gd.small, 0.0, 0, 0, 0};
         double d2 = 0.0, n2 = 0.0, mx = 0.0, ms = 0.0;
+        unsigned long long fxm = 0ull;
         tile_step<L, T, G, TILES>(tg, gd.c, tile - gd.tile_begin, mode, zero_in, lane, grp, sub,
-                                  sbase, xacc, xexp, d2, n2, mx, ms);
+                                  sbase, xacc, xexp, d2, n2, mx, ms, fxm);
         if (mode == kCheck && grp == 0) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -960,6 +1032,8 @@ int variant_count_t() { return Variants<L>::N; }
 
 #define PKR_INSTANTIATE_SWEEP(L)                                                             \
     template int launch_sweep_t<L, double>(int, const SweepArgs&, const void*, int, void*); \
+    template int launch_sweep_t<L, long long>(int, const SweepArgs&, const void*, int, void*); \
+    template int occupancy_t<L, long long>(int, int*, int*);                                 \
     template int launch_sweep_t<L, float>(int, const SweepArgs&, const void*, int, void*);  \
     template int occupancy_t<L, double>(int, int*, int*);                                    \
     template int occupancy_t<L, float>(int, int*, int*);                                     \

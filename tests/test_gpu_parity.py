@@ -400,3 +400,34 @@ def test_tau1_converged_and_mixed(pk):
     mixed, rc2, st2 = _gpu_solve(pk, rho, "D3Q111", 5, 1.0, tol=1e-11, precision="mixed",
                                  max_sweeps=400000)
     assert rc2 == 0 and _rel(mixed, ref.phi) < 1e-8
+
+
+@pytest.mark.parametrize("lattice,order,shape,tau", [
+    ("D3Q111", 5, (9, 7, 13), 1.3), ("D3Q111", 5, (16, 16, 16), 2.5),
+    ("D2Q169", 7, (21, 19), 6.04398), ("D3Q19", 1, (7, 9, 11), 0.75),
+    ("D1Q13", 7, (100,), 1.2), ("D3Q111", 5, (2, 3, 5), 1.4),
+])
+def test_fixed_steps_fx64(pk, lattice, order, shape, tau):
+    """64-bit fixed-point storage: same 1e-12 bar as binary64 (every stored
+    value keeps >= 54 bits relative to the largest; the density sum is exact)."""
+    rho = _rand(shape, 22)
+    for steps in (1, 2, 17):
+        got, rc, st = _gpu_solve(pk, rho, lattice, order, tau, steps=steps, precision="fx64")
+        ref = oracle.solve(rho, lattice, order, tau_lb=tau, max_steps=steps).phi
+        assert rc == 0 and st["sweeps"] == steps
+        assert _rel(got, ref) <= FP64_TOL, (steps, _rel(got, ref))
+
+
+def test_converged_fx64(pk):
+    shape = (12, 10, 14)
+    rho, _ = stiff_source(shape, count=6, sigma=1.5, seed=23)
+    ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.3, tol=1e-10, tol_kind=1, check_every=8,
+                       max_steps=200000)
+    got, rc, st = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-10, check_every=8,
+                             max_sweeps=200000, precision="fx64")
+    assert rc == 0 and st["sweeps"] == ref.steps
+    assert _rel(got, ref.phi) <= FP64_TOL
+    # the fixed-point scale was lowered along the way (values grew ~10^3x)
+    a, _, _ = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-10, check_every=8,
+                         max_sweeps=200000, precision="fx64")
+    assert np.array_equal(a, got)
