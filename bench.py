@@ -43,8 +43,8 @@ WORKLOAD = "poisson3d_256cube_d3q111_n5_fp64_64gauss_sigma2_seed0_kn0.2"
 
 
 def dist_env():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
-        int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1504_05869_gb300 import replicas
+    return replicas.env()
 
 
 def source():
@@ -235,13 +235,12 @@ def run(args):
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
     dev_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([dev_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
-        dist.barrier()
     sweeps = args.steps * SWEEPS_PER_STEP
-    glups = world * V * sweeps / (dev_ms * 1e-3) / 1e9
+    from paper_1504_05869_gb300 import replicas
+    dev_ms, total_updates = replicas.aggregate(dev_ms, float(V) * sweeps, device="cuda")
+    if dist:
+        dist.barrier()
+    glups = total_updates / (dev_ms * 1e-3) / 1e9
     bytes_site = 2 * Q * esize + (8 if PRECISION in ("fp64", "fx64") else 4)
     # per-launch: plain sweeps move 2*Q*8 + 8 bytes per site
     launch_ms = dev_ms / sweeps
@@ -271,11 +270,9 @@ def run(args):
             rc, est = pk.solve(rho_h.numpy(), phi_h.numpy(), eprob, stream=stream)
         torch.cuda.synchronize()
         e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_s = float(t.item())
-        e2e = {"value": world * V * est["launches"] / e_s / 1e9, "unit": "GLUPS",
+        from paper_1504_05869_gb300 import replicas
+        e_s, e_updates = replicas.aggregate(e_s, float(V) * est["launches"], device="cuda")
+        e2e = {"value": e_updates / e_s / 1e9, "unit": "GLUPS",
                "h2d_bytes_per_step": V * 8, "d2h_bytes_per_step": V * 8,
                "solve": {"sweeps": est["sweeps"], "residual": est["residual"],
                          "status": rc, "seconds": e_s, "tol": 1e-10}}
