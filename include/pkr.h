@@ -235,6 +235,35 @@ int pkr_solve(const pkr_problem *problem, const double *rho, double *phi, int ho
               pkr_stats *stats, void *stream);
 
 /* ---------------------------------------------------------------------
+ * Direct comparator: the exact fixed point of the scheme by FFT.
+ *
+ * The time step above (streaming, BGK relaxation to phi_i Phi, source
+ * chi_i S; Sec. "Kinetic approach to the Poisson equation") is linear and
+ * translation invariant on the periodic grid, so its steady state is diagonal
+ * in Fourier space: Phi(k) = T(k) S(k) with
+ *     T(k) = sum_i chi_i q_i / sum_i phi_i (1 - e_i) / (1 - (1 - w) e_i),
+ *     q_i = e_i / (1 - (1 - w) e_i),  e_i = exp(-i k.v_i),  w = 1 / tau_lb,
+ * and Phi(0) = 0.  This is the limit the iteration (pkr_solve with tol -> 0)
+ * converges to -- same lattice, order, tau_lb and source, including the
+ * O(Kn^2) kinetic correction -- so it serves as a direct solver for the
+ * scheme and as an exact reference for its residual.  It is not the Poisson
+ * solution: that is the tau_lb -> 1/2 limit.
+ *
+ * problem: lattice, n, order, tau_lb (or knudsen), epsilon are used; tol,
+ * check_every, max_sweeps, precision and variant are ignored (binary64
+ * throughout).  rho, phi: as pkr_solve (device, or host with host_buffers).
+ * Device memory: V doubles + (nx/2+1) ny nz complex doubles + cuFFT's plan
+ * work area, allocated and freed inside the call.  Synchronises the stream.
+ * stats: rho_mean_removed, tau_lb, cs2, wall_ms (others 0).
+ * Errors (phi untouched on each): PKR_EINVAL (bad problem, V > 2^31 - 1,
+ * tau_lb <= 1/2, non-finite rho), PKR_EUNSTABLE (tau_lb outside the stable
+ * range of the lattice, as pkr_solve), PKR_ENOMEM, PKR_ECUDA (a CUDA or cuFFT
+ * call failed).
+ * --------------------------------------------------------------------- */
+int pkr_fixed_point_fft(const pkr_problem *problem, const double *rho, double *phi,
+                        int host_buffers, pkr_stats *stats, void *stream);
+
+/* ---------------------------------------------------------------------
  * Batches and serving: a context advances many independent periodic solves
  * (same lattice, order and storage) together, one persistent kernel launch
  * per step over all live grids, K steps per captured CUDA graph.  Requests

@@ -94,6 +94,20 @@ def solve(rho, phi, prob, stream=None):
     return rc, st.as_dict()
 
 
+def fixed_point_fft(rho, phi, prob, stream=None):
+    """pkr_fixed_point_fft: the scheme's exact steady state by FFT (direct
+    comparator; same lattice, order, tau_lb and source as ``solve``).
+    Returns the stats dict; raises PkrError on any error."""
+    rp, rh = _ptr(rho)
+    pp, ph = _ptr(phi)
+    if rh != ph:
+        raise ValueError("rho and phi must both be on the device or both on the host")
+    st = pkr_stats()
+    check(_pkr.pkr_fixed_point_fft(ctypes.byref(prob), rp, pp, int(rh), ctypes.byref(st),
+                                   _stream_ptr(stream)), "pkr_fixed_point_fft")
+    return st.as_dict()
+
+
 class Plan:
     """Device-resident solve state (pkr_plan_*)."""
 

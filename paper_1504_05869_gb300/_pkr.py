@@ -32,6 +32,7 @@ EXPORTS = [
     "pkr_plan_populations", "pkr_solve", "pkr_residual_noalloc", "pkr_variant_count",
     "pkr_plan_autotune", "pkr_ctx_create", "pkr_submit", "pkr_poll", "pkr_ctx_run",
     "pkr_ctx_wait", "pkr_ctx_info", "pkr_ctx_destroy", "pkr_plan_import",
+    "pkr_fixed_point_fft",
 ]
 
 
@@ -89,6 +90,8 @@ _SIGS = {
     "pkr_solve": (ctypes.c_int, [ctypes.POINTER(pkr_problem), _P, _P, ctypes.c_int,
                                  ctypes.POINTER(pkr_stats), _P]),
     "pkr_residual_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _D, _P]),
+    "pkr_fixed_point_fft": (ctypes.c_int, [ctypes.POINTER(pkr_problem), _P, _P, ctypes.c_int,
+                                           ctypes.POINTER(pkr_stats), _P]),
     "pkr_variant_count": (ctypes.c_int, [ctypes.c_int]),
     "pkr_plan_autotune": (ctypes.c_int, [_P, ctypes.c_int, _I32, _D]),
     "pkr_ctx_create": (ctypes.c_int, [ctypes.POINTER(pkr_ctx_config), _P, ctypes.POINTER(_P)]),
@@ -157,6 +160,7 @@ pkr_plan_steps = _fn("pkr_plan_steps")
 pkr_plan_populations = _fn("pkr_plan_populations")
 pkr_solve = _fn("pkr_solve")
 pkr_residual_noalloc = _fn("pkr_residual_noalloc")
+pkr_fixed_point_fft = _fn("pkr_fixed_point_fft")
 pkr_variant_count = _fn("pkr_variant_count")
 pkr_plan_autotune = _fn("pkr_plan_autotune")
 pkr_ctx_create = _fn("pkr_ctx_create")

@@ -68,7 +68,9 @@ def build(force: bool = False, verbose: bool = False, jobs: int = 0) -> str:
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + [
+        "-L" + cudalib, "-Xlinker", "-rpath=" + cudalib, "-lcufft"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

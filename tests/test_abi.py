@@ -120,6 +120,27 @@ def test_stability_precheck(pkr):
         pkr._pkr.pkr_plan_destroy(h)
 
 
+def test_fixed_point_fft_validation(pkr):
+    """The FFT comparator checks its problem on the host before any CUDA call."""
+    rho = np.zeros((4, 4, 4))
+    phi = np.zeros((4, 4, 4))
+
+    def call(prob):
+        st = pkr._pkr.pkr_stats()
+        return pkr._pkr.pkr_fixed_point_fft(ctypes.byref(prob), rho.ctypes.data, phi.ctypes.data,
+                                            1, ctypes.byref(st), None)
+    assert call(pkr.problem("D3Q111", (4, 4, 4), 5, tau_lb=0.5)) == -1
+    assert call(pkr.problem("D3Q111", (4, 4, 4), 5, tau_lb=0.6)) == -3
+    assert call(pkr.problem("D3Q111", (4, 4, 4), 9, tau_lb=1.0)) == -1
+    bad = pkr.problem("D3Q111", (4, 4, 4), 5, tau_lb=1.0)
+    bad.dim = 2
+    assert call(bad) == -1
+    st = pkr._pkr.pkr_stats()
+    assert pkr._pkr.pkr_fixed_point_fft(ctypes.byref(bad), None, None, 1, ctypes.byref(st),
+                                        None) == -1
+    assert not phi.any()
+
+
 def test_plan_bytes(pkr):
     p = pkr.problem("D3Q111", (256, 256, 256), 5, tau_lb=1.0)
     b = ctypes.c_size_t()
