@@ -11,7 +11,8 @@ GB) are far larger than L2, so no flush is needed between steps.
 ``e2e``: the same metric for a complete solve to rel. residual 1e-10 through
 ``pkr_solve`` with host buffers (H2D of rho and D2H of Phi inside the timed
 region).  ``cpu_baseline``: the oracle (serial C) on a 64-plane slab of the same
-source.  ``--impl reference`` times that oracle alone, as the reference arm.
+source; ``cpu_baseline_openmp``: the same source built with OpenMP on every host
+core.  ``--impl reference`` times the serial oracle alone, as the reference arm.
 
 Multi-GPU: the path does not shard (one grid per GPU, no collectives), so N
 ranks run N independent replicas; value = all ranks' site updates / the
@@ -153,6 +154,25 @@ def cpu_baseline(rho, tau):
                       f"{SLAB}x256x256 slab of the same source, serial C, {dt:.1f} s"}
 
 
+def cpu_baseline_openmp(rho, tau):
+    """The same oracle source built with OpenMP (the site loop of a step
+    shared by z-plane; bitwise the serial result), on every host core, on
+    the same slab: a second reported baseline."""
+    import oracle
+    try:
+        cores = oracle.threads(len(os.sched_getaffinity(0)))
+    except Exception as e:              # no OpenMP-capable compiler on this host
+        return {"unavailable": f"OpenMP oracle build failed: {e}"[:200]}
+    slab = np.ascontiguousarray(rho[:SLAB])
+    oracle.solve(slab[:4], LATTICE, ORDER, tau_lb=tau, max_steps=1, openmp=True)   # warm-up
+    t0 = time.perf_counter()
+    oracle.solve(slab, LATTICE, ORDER, tau_lb=tau, max_steps=1, openmp=True)
+    dt = time.perf_counter() - t0
+    return {"value": slab.size / dt / 1e9, "unit": "GLUPS", "cores": cores,
+            "kind": "oracle (OpenMP build)",
+            "sample": f"1 step on the same {SLAB}x256x256 slab, {cores} threads, {dt:.2f} s"}
+
+
 def run_reference(args):
     """Reference arm: the oracle timed on the host, each step one oracle step
     on a 2-plane slab of the benchmark's source."""
@@ -277,9 +297,10 @@ def run(args):
                "solve": {"sweeps": est["sweeps"], "residual": est["residual"],
                          "status": rc, "seconds": e_s, "tol": 1e-10}}
 
-    cpu = None
+    cpu = cpu_omp = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(rho, tau)
+        cpu_omp = cpu_baseline_openmp(rho, tau)
 
     if rank == 0:
         line = {
@@ -301,8 +322,8 @@ def run(args):
                          "kernel": f"sweep_staged_kernel<{LATTICE},"
                                    f"{ {'fp64': 'double', 'fx64': 'long long'}.get(PRECISION, 'float') }>",
                          "algorithmic_bytes_per_launch": V * bytes_site},
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": args.steps * (SWEEPS_PER_STEP + 1),
+            "cpu_baseline": cpu, "cpu_baseline_openmp": cpu_omp, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": args.steps * (SWEEPS_PER_STEP + 1),
             "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
@@ -447,10 +468,17 @@ def run_poisson2d(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         got = phi.cpu().numpy()
+        fx = torch.empty_like(r)
+        pk.fixed_point_fft(r, fx, prob)
+        fx = fx.cpu().numpy()
         out[label] = {"status": rc, "sweeps": st["sweeps"], "seconds": dt,
                       "glups": 4096 * st["launches"] / dt / 1e9, "tau_lb": st["tau_lb"],
                       "rel_l2_vs_analytic": float(np.linalg.norm(got - exact) /
-                                                  np.linalg.norm(exact))}
+                                                  np.linalg.norm(exact)),
+                      "rel_l2_vs_scheme_fixed_point": float(np.linalg.norm(got - fx) /
+                                                            np.linalg.norm(fx)),
+                      "fixed_point_vs_analytic": float(np.linalg.norm(fx - exact) /
+                                                       np.linalg.norm(exact))}
     line = {"metric": "time to max|dPhi| < 1e-12, 2D 64^2 D2Q169 N=7", "workload": "poisson2d",
             "value": out["kn0.1"]["seconds"], "unit": "s", "higher_is_better": False,
             "runs": out, "data": "synthetic"}
@@ -541,6 +569,63 @@ def run_precision(args):
     return 0
 
 
+def run_knudsen(args):
+    """The 256^3 stiff-source problem (64 Gaussians, sigma 2, seed 0) solved
+    in binary64 to rel. L2 residual 1e-10 at Kn 0.05, 0.2 and 0.5, with the
+    N=5 3D set and with standard first-order LB (D3Q19, N=1).  Each run
+    reports its sweeps, wall time and GLUPS, its distance to the scheme's
+    exact fixed point (FFT comparator) and that fixed point's distance to
+    the continuum periodic Poisson solution (spectral, reported only)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+    rho = source()
+    r = torch.from_numpy(rho).cuda()
+    # continuum: Phi(k) = rho(k) / |k|^2 (eps = 1), Phi(0) = 0
+    ks = [2 * np.pi * torch.fft.fftfreq(n, device="cuda", dtype=torch.float64) for n in SHAPE]
+    k2 = ks[0][:, None, None] ** 2 + ks[1][None, :, None] ** 2 + ks[2][None, None, :] ** 2
+    k2[0, 0, 0] = 1.0
+    rk = torch.fft.fftn(r - r.mean()) / k2
+    rk[0, 0, 0] = 0.0
+    cont = torch.fft.ifftn(rk).real
+    del rk, k2
+    ncont = torch.linalg.norm(cont).item()
+    out = {}
+    for lattice, order in (("D3Q111", 5), ("D3Q19", 1)):
+        stream = torch.cuda.Stream()
+        with pk.Plan(pk.problem(lattice, SHAPE, order, knudsen=0.2, max_sweeps=10 ** 6),
+                     stream=stream) as P:
+            P.load_source(r)
+            variant, _ = P.autotune(4)
+        torch.cuda.empty_cache()
+        for kn in (0.05, 0.2, 0.5):
+            prob = pk.problem(lattice, SHAPE, order, knudsen=kn, tol=1e-10, tol_kind="rel_l2",
+                              check_every=SWEEPS_PER_STEP, max_sweeps=200000, variant=variant)
+            phi = torch.empty_like(r)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, st = pk.solve(r, phi, prob)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            fx = torch.empty_like(r)
+            fst = pk.fixed_point_fft(r, fx, prob)
+            nfx = torch.linalg.norm(fx).item()
+            out[f"{lattice}_kn{kn}"] = {
+                "status": rc, "tau_lb": st["tau_lb"], "sweeps": st["sweeps"], "seconds": dt,
+                "glups": r.numel() * st["launches"] / dt / 1e9, "variant": variant,
+                "rel_l2_vs_scheme_fixed_point": torch.linalg.norm(phi - fx).item() / nfx,
+                "fixed_point_seconds": fst["wall_ms"] / 1e3,
+                "fixed_point_vs_continuum": torch.linalg.norm(fx - cont).item() / ncont}
+            del phi, fx
+            torch.cuda.empty_cache()
+    line = {"metric": "binary64 solve to rel. L2 residual 1e-10 at 256^3, Kn 0.05/0.2/0.5",
+            "workload": "knudsen", "value": out["D3Q111_kn0.2"]["seconds"], "unit": "s",
+            "higher_is_better": False, "runs": out, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_tau1(args):
     """The paper's setting tau_lb = 1 (D3Q111 N=5): the scalar-stencil path
     against the population sweep, per step at 256^3 (64 Gaussians) and for a
@@ -604,7 +689,8 @@ def main():
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16", "fx64"])
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "batch", "serve", "poisson2d", "precision", "tau1"])
+                    choices=["sweep", "batch", "serve", "poisson2d", "precision", "tau1",
+                             "knudsen"])
     ap.add_argument("--no-512", action="store_true")
     ap.add_argument("--target-tol", type=float, default=1e-10)
     ap.add_argument("--batch-count", type=int, default=256)
@@ -623,6 +709,8 @@ def main():
         return run_precision(args)
     if args.workload == "tau1":
         return run_tau1(args)
+    if args.workload == "knudsen":
+        return run_knudsen(args)
     configure(args)
     if args.impl == "reference":
         return run_reference(args)

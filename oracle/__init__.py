@@ -13,4 +13,4 @@ instead.
 """
 from .lattice import LATTICES, MAX_ORDER, Lattice, lattice  # noqa: F401
 from .oracle import (Result, build, density, grid3, solve, source, step,  # noqa: F401
-                     tau_from_knudsen)
+                     tau_from_knudsen, threads)

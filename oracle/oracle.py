@@ -24,29 +24,34 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pkr_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
-_lib = None
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+_libs = {}
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)
 _I32 = ctypes.POINTER(ctypes.c_int32)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into a shared library (no-op when up to date)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle into a shared library (no-op when up to date).
+    ``openmp`` builds the multi-core baseline from the same source."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (force or not os.path.exists(_LIB)
-            or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)):
-        tmp = _LIB + f".{os.getpid()}.tmp"
+    out = _LIB_OMP if openmp else _LIB
+    if (force or not os.path.exists(out)
+            or os.path.getmtime(out) < os.path.getmtime(_SRC)):
+        tmp = out + f".{os.getpid()}.tmp"
+        extra = ["-fopenmp"] if openmp else []
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC",
-                               "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               "-shared", "-std=c11"] + extra + [_SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+def _load(openmp: bool = False):
+    if openmp not in _libs:
+        lib = ctypes.CDLL(build(openmp=openmp))
+        lib.oracle_threads.restype = ctypes.c_int
+        lib.oracle_threads.argtypes = [ctypes.c_int]
         lib.oracle_source.restype = ctypes.c_double
         lib.oracle_source.argtypes = [ctypes.c_int64, _D, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, _D]
@@ -62,8 +67,14 @@ def _load():
                                      ctypes.c_double, _D, ctypes.c_double,
                                      ctypes.c_int, ctypes.c_int64,
                                      ctypes.c_int64, _D, _D, _D]
-        _lib = lib
-    return _lib
+        _libs[openmp] = lib
+    return _libs[openmp]
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the OpenMP build's step (sets it when n > 0); returns the
+    count in effect."""
+    return int(_load(True).oracle_threads(int(n)))
 
 
 def _dp(a: np.ndarray):
@@ -112,14 +123,16 @@ def _tables(lat: Lattice):
     return (vel, np.ascontiguousarray(lat.phi), np.ascontiguousarray(lat.chi))
 
 
-def step(g: np.ndarray, S: np.ndarray, lat: Lattice, omega: float) -> np.ndarray:
-    """One collide-and-stream step of the state g (shape (Q,) + grid)."""
+def step(g: np.ndarray, S: np.ndarray, lat: Lattice, omega: float,
+         openmp: bool = False) -> np.ndarray:
+    """One collide-and-stream step of the state g (shape (Q,) + grid);
+    ``openmp`` runs the multi-core build (bitwise the same result)."""
     n = np.array(grid3(S.shape), dtype=np.int64)
     vel, phi, chi = _tables(lat)
     gi = np.ascontiguousarray(g, dtype=np.float64)
     go = np.empty_like(gi)
     Sc = np.ascontiguousarray(S, dtype=np.float64)
-    _load().oracle_step(n.ctypes.data_as(_I64), lat.Q, vel.ctypes.data_as(_I32),
+    _load(openmp).oracle_step(n.ctypes.data_as(_I64), lat.Q, vel.ctypes.data_as(_I32),
                         _dp(phi), _dp(chi), float(omega), _dp(Sc), _dp(gi), _dp(go))
     return go
 
@@ -137,13 +150,14 @@ class Result:
 def solve(rho: np.ndarray, lattice_name: str, order: int, tau_lb: float = None,
           knudsen: float = None, eps: float = 1.0, tol: float = 0.0,
           tol_kind: int = 1, check_every: int = 1, max_steps: int = 1000,
-          g0: np.ndarray = None, S: np.ndarray = None) -> Result:
+          g0: np.ndarray = None, S: np.ndarray = None, openmp: bool = False) -> Result:
     """Run the scheme from g = 0 (or g0).
 
     tol <= 0 runs exactly ``max_steps`` steps.  tol_kind 0 stops on
     max|dPhi| < tol, 1 on ||dPhi||_2/||Phi||_2 < tol, checked every
     ``check_every`` steps.  If S is given it is used as the source directly
-    (no mean removal, no scaling).
+    (no mean removal, no scaling).  ``openmp`` runs the multi-core build
+    (bitwise the same result).
     """
     lat = lattice(lattice_name, order)
     n3 = grid3(rho.shape)
@@ -161,7 +175,7 @@ def solve(rho: np.ndarray, lattice_name: str, order: int, tau_lb: float = None,
     res = ctypes.c_double(0.0)
     vel, phi, chi = _tables(lat)
     n = np.array(n3, dtype=np.int64)
-    t = _load().oracle_solve(n.ctypes.data_as(_I64), lat.Q,
+    t = _load(openmp).oracle_solve(n.ctypes.data_as(_I64), lat.Q,
                              vel.ctypes.data_as(_I32), _dp(phi), _dp(chi),
                              1.0 / float(tau_lb), _dp(S), float(tol),
                              int(tol_kind), int(check_every), int(max_steps),

@@ -28,11 +28,33 @@
  *       g_i(x+v_i)  = p_i(x)                      (streaming, periodic)
  *
  * Layout: g[i*V + (z*ny + y)*nx + x], V = nx*ny*nz.
+ *
+ * The same file also builds, with -fopenmp, the multi-core CPU baseline: the
+ * site loop of a step is shared among threads by z-plane.  Every site's
+ * arithmetic and every written address are unchanged (each (i, x) pushes to
+ * its own destination), so the result is bitwise the serial one.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads used by oracle_step: sets the count when n > 0 (OpenMP build
+ * only) and returns the count in effect (1 for the serial build). */
+int oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 static int64_t wrap(int64_t a, int64_t n)
 {
@@ -73,6 +95,9 @@ void oracle_step(const int64_t n[3], int Q, const int32_t *vel,
 {
     const int64_t nx = n[0], ny = n[1], nz = n[2];
     const int64_t V = nx * ny * nz;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t z = 0; z < nz; ++z)
         for (int64_t y = 0; y < ny; ++y)
             for (int64_t x = 0; x < nx; ++x) {

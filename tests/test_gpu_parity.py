@@ -431,3 +431,21 @@ def test_converged_fx64(pk):
     a, _, _ = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-10, check_every=8,
                          max_sweeps=200000, precision="fx64")
     assert np.array_equal(a, got)
+
+
+@pytest.mark.parametrize("tau,precision", [(1.3, "fp64"), (1.0, "fp64"), (1.3, "fp32")])
+def test_overflowing_source_reports_divergence(pk, tau, precision):
+    """A permittivity so small that the source overflows to +-inf makes the
+    populations and the residual non-finite: the solve stops at its next
+    check with PKR_EDIVERGED (tau_lb = 1 exercises the scalar-stencil path)
+    and leaves Phi untouched."""
+    import torch
+    rho = _rand((8, 9, 10), 3)
+    prob = pk.problem("D3Q111", rho.shape, 5, tau_lb=tau, epsilon=1e-320, tol=1e-10,
+                      check_every=4, max_sweeps=64, precision=precision)
+    r = torch.from_numpy(rho).cuda()
+    phi = torch.full_like(r, 7.0)
+    with pytest.raises(pk.PkrError) as e:
+        pk.solve(r, phi, prob)
+    assert e.value.status == -5
+    assert bool((phi == 7.0).all())

@@ -260,3 +260,25 @@ def test_small_tau_instability():
     bad = solve(rho, "D3Q111", 5, tau_lb=0.6, max_steps=300)
     good = solve(rho, "D3Q111", 5, tau_lb=1.0, max_steps=300)
     assert np.abs(bad.phi).max() > 1e6 * np.abs(good.phi).max()
+
+
+def test_openmp_build_is_bitwise_serial():
+    """The multi-core baseline build (same source, -fopenmp) gives exactly the
+    serial oracle's result: each site's arithmetic is unchanged and every
+    push goes to its own address."""
+    import oracle
+    try:
+        n = oracle.threads(3)
+    except Exception as e:      # compiler without OpenMP support
+        pytest.skip(f"OpenMP build unavailable: {e}")
+    assert n == 3
+    lat = lattice("D3Q111", 5)
+    rho = _rand_source((7, 9, 10), 8)
+    S, _ = source(rho, lat, 1.3)
+    g = np.random.default_rng(9).standard_normal((lat.Q,) + rho.shape)
+    a = step(g, S, lat, 1 / 1.3)
+    b = step(g, S, lat, 1 / 1.3, openmp=True)
+    assert np.array_equal(a, b)
+    r1 = solve(rho, "D3Q111", 5, tau_lb=1.3, max_steps=5)
+    r2 = solve(rho, "D3Q111", 5, tau_lb=1.3, max_steps=5, openmp=True)
+    assert np.array_equal(r1.phi, r2.phi)
