@@ -61,6 +61,8 @@ def configure(args):
     if args.size:
         SHAPE = (args.size,) * 3
     LATTICE, ORDER, PRECISION = args.lattice, args.order, args.precision
+    if PRECISION == "mixed":
+        raise SystemExit("--precision mixed applies to the batch and serve workloads")
     if (SHAPE, LATTICE, ORDER, PRECISION) != ((256, 256, 256), "D3Q111", 5, "fp64"):
         n = SHAPE[0]
         WORKLOAD = (f"poisson3d_{n}cube_{LATTICE.lower()}_n{ORDER}_{PRECISION}"
@@ -354,7 +356,7 @@ def run_batch(args):
     import paper_1504_05869_gb300 as pk
     from paper_1504_05869_gb300.workloads import batch_jobs
     jobs = batch_jobs(args.batch_count, seed=2)
-    tol = args.tol if args.tol > 0 else (1e-8 if args.precision == "fp64" else 1e-7)
+    tol = args.tol if args.tol > 0 else (1e-7 if args.precision == "fp32" else 1e-8)
     rhos = [torch.from_numpy(j.rho()).cuda() for j in jobs]
     phis = [torch.zeros_like(r) for r in rhos]
     torch.cuda.synchronize()
@@ -374,12 +376,19 @@ def run_batch(args):
     ok = sum(1 for rc, _ in stats if rc == 0)
     sweeps = [st["sweeps"] for rc, st in stats if st]
     sites = sum(r.numel() for r in rhos)
+    # distance of the first grids' results to their exact fixed points (FFT comparator)
+    errs = []
+    for j, r, p in list(zip(jobs, rhos, phis))[:16]:
+        fx = torch.empty_like(r)
+        pk.fixed_point_fft(r, fx, pk.problem("D3Q111", r.shape, 5, knudsen=KN))
+        errs.append(torch.linalg.norm(p - fx).item() / torch.linalg.norm(fx).item())
     line = {"metric": "batched solves: GLUPS over all grids and solves/s", "workload": "batch",
             "value": info["site_updates"] / dt / 1e9, "unit": "GLUPS",
             "solves_per_s": ok / dt, "solves": len(jobs), "converged": ok, "seconds": dt,
             "sites_total": sites, "site_updates": info["site_updates"],
             "sweeps_min_median_max": [min(sweeps), _pct(sweeps, 50), max(sweeps)],
             "precision": args.precision, "tol_rel_l2": tol, "kernel_variant": info["variant"],
+            "rel_l2_vs_fixed_point_first16": {"median": _pct(errs, 50), "max": max(errs)},
             "windows": info["windows"], "check_every": SWEEPS_PER_STEP,
             "hbm_budget_gb": args.budget_gb, "data": "synthetic",
             "config": {"grids": len(jobs), "edges": "log-uniform [32,128], seed 2",
@@ -687,7 +696,9 @@ def main():
     ap.add_argument("--size", type=int, default=0, help="cube edge (default 256)")
     ap.add_argument("--lattice", default="D3Q111", choices=["D3Q111", "D3Q19"])
     ap.add_argument("--order", type=int, default=5)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16", "fx64"])
+    ap.add_argument("--precision", default="fp64",
+                    choices=["fp64", "fp32", "fp16", "fx64", "mixed"],
+                    help="sweep workload: fp64/fp32/fp16/fx64; batch/serve: fp64/fp32/mixed")
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "batch", "serve", "poisson2d", "precision", "tau1",
                              "knudsen"])

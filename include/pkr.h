@@ -66,7 +66,7 @@ typedef enum pkr_lattice {
  * Phi, so binary32 alone cannot meet tighter tolerances.  binary32 rounding
  * does not conserve the mass sum_x Phi; plans remove the drift at every
  * residual check (through the source of the next step).
- * MIXED (pkr_solve only): binary32 steps until the per-step change falls
+ * MIXED (pkr_solve and contexts): binary32 steps until the per-step change falls
  * below PKR_MIXED_SWITCH_TOL (or tol, if looser), then the state is
  * converted to binary64 and binary64 steps continue to tol.  The binary64
  * iteration converges to the binary64 fixed point from any start, so the
@@ -271,13 +271,22 @@ int pkr_fixed_point_fft(const pkr_problem *problem, const double *rho, double *p
  * the next K-step boundary, and retire when their own residual check (every
  * K steps of their own age) passes; the freed memory admits the next ones.
  * A grid's result does not depend on what else is in the batch.
+ * A PKR_MIXED context keeps two batches, binary32 and binary64: a request
+ * starts in binary32 and, at the check where its residual falls below
+ * PKR_MIXED_SWITCH_TOL (or stops falling, at the binary32 rounding floor),
+ * its state is converted to binary64 (projected onto the zero-mass gauge)
+ * and it continues in the binary64 batch to its tolerance, with its step
+ * count and check schedule unchanged.  Requests with tol >= the switch
+ * tolerance finish in binary32.  Its budget reservation per request is the
+ * binary32 state + the binary64 state + Phi (both states exist while it is
+ * converted); the binary32 share is released at the switch.
  * --------------------------------------------------------------------- */
 typedef struct pkr_ctx pkr_ctx;
 
 typedef struct pkr_ctx_config {
     int32_t lattice;          /* pkr_lattice of every request */
     int32_t order;            /* expansion order N of every request */
-    int32_t precision;        /* pkr_precision of every request */
+    int32_t precision;        /* PKR_FP64, PKR_FP32 or PKR_MIXED, for every request */
     int32_t check_every;      /* K: steps per graph replay and per residual check (>= 1) */
     size_t hbm_budget_bytes;  /* device bytes the live requests may hold */
     int32_t variant;          /* >= 0: kernel geometry; -1: library default;

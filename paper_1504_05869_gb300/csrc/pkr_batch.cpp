@@ -9,6 +9,12 @@
 // context's stream; they start at the window boundary) and retires the grids
 // whose check at the end of the window passed.  A worker thread drives the
 // windows in threaded contexts; pkr_ctx_run does in the others.
+//
+// A MIXED context runs two such batches ("lanes"): binary32 and binary64.
+// Requests start in the binary32 lane; when a request's own residual passes
+// PKR_MIXED_SWITCH_TOL (or stops falling at the binary32 rounding floor) its
+// state is converted to binary64 and it continues in the binary64 lane, with
+// its age and check schedule unchanged, until its tolerance.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -97,16 +103,36 @@ struct Job {
     int host = 0;
     int status = PKR_EBUSY;
     pkr_stats st{};
-    void* pop[2] = {nullptr, nullptr};
-    void* S = nullptr;
-    double* Phi = nullptr;
-    size_t bytes = 0;
+    void* pop[2] = {nullptr, nullptr};   // populations in the precision of the job's lane
+    void* S = nullptr;                   // source, same precision
+    double* Phi = nullptr;               // density (binary64)
+    size_t bytes = 0;                    // bytes counted against the budget (reservation)
     int64_t V = 0;
     int ntiles = 0;
-    long long join = 0;
+    int lane = 0;                        // 0: first (or only) lane; 1: binary64 lane of MIXED
+    long long join = 0;                  // lane step at which the job's age was 0
     double tau = 0, omega = 0, mean = 0;
+    double prev_res = INFINITY;          // residual at the previous check (binary32 lane)
     double t_submit = 0;
     int small = 0;
+};
+
+// One batch of grids stored in one precision, advanced by one persistent
+// kernel per step and one captured graph per window.
+struct Lane {
+    int prec = PKR_FP32, elem = 4, grid_stride = 0, variant = 0, grid = 0;
+    BatchState* d_state = nullptr;
+    BatchState h_state{};
+    unsigned char* d_grids = nullptr;
+    std::vector<unsigned char> h_grids;
+    double* d_tile_partials = nullptr;
+    int64_t tiles_cap = 0;
+    double* d_res = nullptr;
+    double* h_res = nullptr;   // pinned, 3 per grid slot
+    cudaGraphExec_t graph = nullptr;
+    long long step = 0;
+    bool dirty = true;
+    std::vector<Job*> live;
 };
 
 }  // namespace
@@ -115,34 +141,23 @@ struct pkr_ctx {
     pkr_ctx_config cfg{};
     LatticeInfo li{};
     cudaStream_t stream = nullptr;
-    int device = 0, nsm = 0, elem = 8, variant = 0, grid = 0, K = 32, max_grids = 4096;
+    int device = 0, nsm = 0, K = 32, max_grids = 4096;
+    bool mixed = false;
     size_t budget = 0, used = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::thread worker;
     bool stop = false;
     std::deque<Job*> queue;
-    std::vector<Job*> live;
     std::map<uint64_t, Job*> jobs;
     uint64_t next_ticket = 1;
-    // device state
-    BatchState* d_state = nullptr;
-    BatchState h_state{};
-    unsigned char* d_grids = nullptr;
-    std::vector<unsigned char> h_grids;
-    int grid_stride = 0;
-    double* d_tile_partials = nullptr;
-    int64_t tiles_cap = 0;
-    double* d_res = nullptr;
-    double* h_res = nullptr;   // pinned, 3 per grid slot
+    Lane lane[2];
+    int nlanes = 1;
     double* d_scratch = nullptr;
     int* d_flag = nullptr;
     double* d_mean = nullptr;
     int* h_flag = nullptr;     // pinned
     double* h_mean = nullptr;  // pinned
-    cudaGraphExec_t graph = nullptr;
-    long long step = 0;
-    bool dirty = true;
     int64_t finished = 0, windows = 0;
     double site_updates = 0;
 };
@@ -174,19 +189,35 @@ void fill_grid(unsigned char* dst, const Job* j, const LatticeInfo& li, int tile
     std::memcpy(dst, &g, sizeof(g));
 }
 
-size_t job_bytes(const pkr_ctx* C, int64_t V)
+// Populations and source of one grid in one lane's precision.
+size_t lane_bytes(const pkr_ctx* C, int ln, int64_t V)
 {
-    const size_t e = (size_t)C->elem;
-    return 2 * (size_t)C->li.Q * (size_t)V * e + (size_t)V * e + (size_t)V * 8;
+    const size_t e = (size_t)C->lane[ln].elem;
+    return 2 * (size_t)C->li.Q * (size_t)V * e + (size_t)V * e;
 }
 
-void free_job_memory(pkr_ctx* C, Job* j)
+// Budget reservation of a request: its lane-0 state plus Phi; in a MIXED
+// context also its binary64 state, which coexists with the binary32 one
+// while the state is converted.
+size_t job_bytes(const pkr_ctx* C, int64_t V)
+{
+    size_t b = lane_bytes(C, 0, V) + (size_t)V * 8;
+    if (C->mixed) b += lane_bytes(C, 1, V);
+    return b;
+}
+
+void free_lane_state(pkr_ctx* C, Job* j)
 {
     for (int k = 0; k < 2; ++k)
         if (j->pop[k]) cudaFreeAsync(j->pop[k], C->stream);
     if (j->S) cudaFreeAsync(j->S, C->stream);
-    if (j->Phi) cudaFreeAsync(j->Phi, C->stream);
     j->pop[0] = j->pop[1] = j->S = nullptr;
+}
+
+void free_job_memory(pkr_ctx* C, Job* j)
+{
+    free_lane_state(C, j);
+    if (j->Phi) cudaFreeAsync(j->Phi, C->stream);
     j->Phi = nullptr;
     C->used -= j->bytes;
     j->bytes = 0;
@@ -200,28 +231,50 @@ void finish(pkr_ctx* C, Job* j, int status)
     C->cv_done.notify_all();
 }
 
-// Allocate and prepare a request (context stream; caller holds the lock).
-// Returns PKR_OK, PKR_ENOMEM (try later) or a final error status.
-int admit(pkr_ctx* C, Job* j)
+// Allocate the populations and source of a job in lane ln's precision.
+bool alloc_lane_state(pkr_ctx* C, Job* j, int ln)
 {
-    const size_t b = job_bytes(C, j->V);
-    const size_t popb = (size_t)C->li.Q * (size_t)j->V * (size_t)C->elem;
+    const size_t popb = (size_t)C->li.Q * (size_t)j->V * (size_t)C->lane[ln].elem;
     if (cudaMallocAsync(&j->pop[0], popb, C->stream) != cudaSuccess ||
         cudaMallocAsync(&j->pop[1], popb, C->stream) != cudaSuccess ||
-        cudaMallocAsync(&j->S, (size_t)j->V * C->elem, C->stream) != cudaSuccess ||
-        cudaMallocAsync((void**)&j->Phi, (size_t)j->V * 8, C->stream) != cudaSuccess) {
+        cudaMallocAsync(&j->S, (size_t)j->V * C->lane[ln].elem, C->stream) != cudaSuccess) {
         cudaGetLastError();
-        j->bytes = 0;
-        for (int k = 0; k < 2; ++k)
-            if (j->pop[k]) cudaFreeAsync(j->pop[k], C->stream);
-        if (j->S) cudaFreeAsync(j->S, C->stream);
-        if (j->Phi) cudaFreeAsync(j->Phi, C->stream);
-        j->pop[0] = j->pop[1] = j->S = nullptr;
-        j->Phi = nullptr;
+        free_lane_state(C, j);
+        return false;
+    }
+    return true;
+}
+
+// S = (rho - <rho>) c_s^2 (tau_lb - 1/2) / eps in lane ln's precision, from
+// rho on the device (rd); the mean goes to C->h_mean.  Synchronises.
+int make_job_source(pkr_ctx* C, Job* j, const double* rd, int ln)
+{
+    const double scale = C->li.cs2 * (j->tau - 0.5) / j->prob.epsilon;
+    if (cudaMemsetAsync(C->d_flag, 0, sizeof(int), C->stream) != cudaSuccess ||
+        launch_rho_partials(rd, j->V, C->d_scratch, kScratchBlocks, C->d_flag, C->stream) != 0 ||
+        launch_finalize_mean(C->d_scratch, kScratchBlocks, j->V, C->d_mean, C->stream) != 0 ||
+        launch_make_source(rd, C->d_mean, scale, j->V, j->S, C->lane[ln].prec, C->stream) != 0 ||
+        cudaMemcpyAsync(C->h_flag, C->d_flag, sizeof(int), cudaMemcpyDeviceToHost, C->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(C->h_mean, C->d_mean, sizeof(double), cudaMemcpyDeviceToHost,
+                        C->stream) != cudaSuccess ||
+        cudaStreamSynchronize(C->stream) != cudaSuccess)
+        return PKR_ECUDA;
+    return *C->h_flag ? PKR_EINVAL : PKR_OK;
+}
+
+// Allocate and prepare a request in lane 0 (context stream; caller holds
+// the lock).  Returns PKR_OK, PKR_ENOMEM (try later) or a final error status.
+int admit(pkr_ctx* C, Job* j)
+{
+    if (!alloc_lane_state(C, j, 0)) return PKR_ENOMEM;
+    if (cudaMallocAsync((void**)&j->Phi, (size_t)j->V * 8, C->stream) != cudaSuccess) {
+        cudaGetLastError();
+        free_lane_state(C, j);
         return PKR_ENOMEM;
     }
-    j->bytes = b;
-    C->used += b;
+    j->bytes = job_bytes(C, j->V);
+    C->used += j->bytes;
     const double* rd = j->rho;
     if (j->host) {
         if (cudaMemcpyAsync(j->Phi, j->rho, (size_t)j->V * 8, cudaMemcpyHostToDevice,
@@ -229,168 +282,203 @@ int admit(pkr_ctx* C, Job* j)
             return PKR_ECUDA;
         rd = j->Phi;
     }
-    const double scale = C->li.cs2 * (j->tau - 0.5) / j->prob.epsilon;
-    if (cudaMemsetAsync(C->d_flag, 0, sizeof(int), C->stream) != cudaSuccess ||
-        launch_rho_partials(rd, j->V, C->d_scratch, kScratchBlocks, C->d_flag, C->stream) != 0 ||
+    int rc = make_job_source(C, j, rd, 0);
+    if (rc != PKR_OK) return rc;
+    if (cudaMemsetAsync(j->Phi, 0, (size_t)j->V * 8, C->stream) != cudaSuccess) return PKR_ECUDA;
+    j->mean = *C->h_mean;
+    j->lane = 0;
+    j->join = C->lane[0].step;
+    return PKR_OK;
+}
+
+// MIXED: move a job from the binary32 lane to the binary64 lane at a window
+// boundary.  The state the next step reads is converted to binary64 and
+// projected onto the zero-mass gauge (with c the mean of the latest Phi,
+// c phi_i is subtracted from every population and c from Phi: the k = 0
+// equilibrium mode, sum_i phi_i = 1), which removes the mass drift of the
+// binary32 steps; the source is rebuilt in binary64 from rho.  The job keeps
+// its age, so its check schedule and step count continue.  Its reservation
+// already covers both states.  Caller holds the lock.
+int promote(pkr_ctx* C, Job* j)
+{
+    Lane& L0 = C->lane[0];
+    Lane& L1 = C->lane[1];
+    const long long age = L0.step - j->join;   // age of the next step
+    const int cur = (int)(age & 1);
+    void* old_pop[2] = {j->pop[0], j->pop[1]};
+    void* old_S = j->S;
+    j->pop[0] = j->pop[1] = j->S = nullptr;
+    if (!alloc_lane_state(C, j, 1)) {
+        j->pop[0] = old_pop[0];
+        j->pop[1] = old_pop[1];
+        j->S = old_S;
+        return PKR_ENOMEM;
+    }
+    int rc = PKR_OK;
+    // mean of Phi, then the shift table c phi_i
+    if (launch_rho_partials(j->Phi, j->V, C->d_scratch, kScratchBlocks, C->d_flag, C->stream) !=
+            0 ||
         launch_finalize_mean(C->d_scratch, kScratchBlocks, j->V, C->d_mean, C->stream) != 0 ||
-        launch_make_source(rd, C->d_mean, scale, j->V, j->S, C->cfg.precision, C->stream) != 0 ||
-        cudaMemcpyAsync(C->h_flag, C->d_flag, sizeof(int), cudaMemcpyDeviceToHost, C->stream) !=
-            cudaSuccess ||
         cudaMemcpyAsync(C->h_mean, C->d_mean, sizeof(double), cudaMemcpyDeviceToHost,
                         C->stream) != cudaSuccess ||
-        cudaMemsetAsync(j->Phi, 0, (size_t)j->V * 8, C->stream) != cudaSuccess ||
         cudaStreamSynchronize(C->stream) != cudaSuccess)
-        return PKR_ECUDA;
-    if (*C->h_flag) return PKR_EINVAL;
-    j->mean = *C->h_mean;
-    j->join = C->step;
+        rc = PKR_ECUDA;
+    if (rc == PKR_OK) {
+        const double c = std::isfinite(*C->h_mean) ? *C->h_mean : 0.0;
+        std::vector<double> shift(C->li.Q);
+        for (int i = 0; i < C->li.Q; ++i) shift[i] = c * C->li.phi[i];
+        if (cudaMemcpyAsync(C->d_scratch, shift.data(), shift.size() * 8, cudaMemcpyHostToDevice,
+                            C->stream) != cudaSuccess ||
+            launch_convert_shift(old_pop[cur], PKR_FP32, j->pop[cur], PKR_FP64, C->li.Q, j->V,
+                                 C->d_scratch, C->stream) != 0 ||
+            launch_make_source(j->Phi, C->d_mean, 1.0, j->V, j->Phi, PKR_FP64, C->stream) != 0 ||
+            cudaStreamSynchronize(C->stream) != cudaSuccess)
+            rc = PKR_ECUDA;
+    }
+    if (rc == PKR_OK) {
+        // binary64 source from rho (host rho staged in the array the next step writes)
+        const double* rd = j->rho;
+        if (j->host) {
+            if (cudaMemcpyAsync(j->pop[cur ^ 1], j->rho, (size_t)j->V * 8,
+                                cudaMemcpyHostToDevice, C->stream) != cudaSuccess)
+                rc = PKR_ECUDA;
+            rd = static_cast<const double*>(j->pop[cur ^ 1]);
+        }
+        if (rc == PKR_OK) rc = make_job_source(C, j, rd, 1);
+    }
+    // the binary32 state goes in every case (on an error the job fails with
+    // the binary64 arrays, which free_job_memory releases)
+    for (int k = 0; k < 2; ++k) cudaFreeAsync(old_pop[k], C->stream);
+    cudaFreeAsync(old_S, C->stream);
+    if (rc != PKR_OK) return rc;
+    // release the binary32 share of the reservation
+    C->used -= lane_bytes(C, 0, j->V);
+    j->bytes -= lane_bytes(C, 0, j->V);
+    j->lane = 1;
+    j->join = L1.step - age;
+    L1.live.push_back(j);
+    L1.dirty = true;
     return PKR_OK;
 }
 
-// Upload the descriptors of the live grids (and grow the tile partials).
-int rebuild(pkr_ctx* C)
+// Upload the descriptors of a lane's live grids (and grow its tile partials).
+int rebuild(pkr_ctx* C, Lane& L)
 {
     int64_t tiles = 0;
-    for (Job* j : C->live) tiles += j->ntiles;
+    for (Job* j : L.live) tiles += j->ntiles;
     if (tiles > 0x7fffffff) return PKR_EINVAL;
-    if (tiles > C->tiles_cap) {
-        if (C->d_tile_partials) cudaFreeAsync(C->d_tile_partials, C->stream);
-        C->d_tile_partials = nullptr;
+    if (tiles > L.tiles_cap) {
+        if (L.d_tile_partials) cudaFreeAsync(L.d_tile_partials, C->stream);
+        L.d_tile_partials = nullptr;
         int64_t cap = tiles + tiles / 4 + 1024;
-        if (cudaMallocAsync((void**)&C->d_tile_partials, (size_t)cap * 3 * sizeof(double),
+        if (cudaMallocAsync((void**)&L.d_tile_partials, (size_t)cap * 3 * sizeof(double),
                             C->stream) != cudaSuccess) {
-            C->tiles_cap = 0;
+            L.tiles_cap = 0;
             return PKR_ENOMEM;
         }
-        C->tiles_cap = cap;
+        L.tiles_cap = cap;
     }
     int tb = 0;
-    for (size_t k = 0; k < C->live.size(); ++k) {
-        unsigned char* dst = C->h_grids.data() + k * (size_t)C->grid_stride;
-        if (C->cfg.precision == PKR_FP64) fill_grid<double>(dst, C->live[k], C->li, tb);
-        else fill_grid<float>(dst, C->live[k], C->li, tb);
-        tb += C->live[k]->ntiles;
+    for (size_t k = 0; k < L.live.size(); ++k) {
+        unsigned char* dst = L.h_grids.data() + k * (size_t)L.grid_stride;
+        if (L.prec == PKR_FP64) fill_grid<double>(dst, L.live[k], C->li, tb);
+        else fill_grid<float>(dst, L.live[k], C->li, tb);
+        tb += L.live[k]->ntiles;
     }
-    C->h_state.grids = C->d_grids;
-    C->h_state.tile_partials = C->d_tile_partials;
-    C->h_state.grid_res = C->d_res;
-    C->h_state.step = C->step;
-    C->h_state.ngrids = (int)C->live.size();
-    C->h_state.ntiles = (int)tiles;
-    if (!C->live.empty() &&
-        cudaMemcpyAsync(C->d_grids, C->h_grids.data(), C->live.size() * (size_t)C->grid_stride,
+    L.h_state.grids = L.d_grids;
+    L.h_state.tile_partials = L.d_tile_partials;
+    L.h_state.grid_res = L.d_res;
+    L.h_state.step = L.step;
+    L.h_state.ngrids = (int)L.live.size();
+    L.h_state.ntiles = (int)tiles;
+    if (!L.live.empty() &&
+        cudaMemcpyAsync(L.d_grids, L.h_grids.data(), L.live.size() * (size_t)L.grid_stride,
                         cudaMemcpyHostToDevice, C->stream) != cudaSuccess)
         return PKR_ECUDA;
-    if (cudaMemcpyAsync(C->d_state, &C->h_state, sizeof(BatchState), cudaMemcpyHostToDevice,
+    if (cudaMemcpyAsync(L.d_state, &L.h_state, sizeof(BatchState), cudaMemcpyHostToDevice,
                         C->stream) != cudaSuccess ||
         cudaStreamSynchronize(C->stream) != cudaSuccess)
         return PKR_ECUDA;
-    C->dirty = false;
+    L.dirty = false;
     return PKR_OK;
 }
 
-// Queue one window (K steps + reduction + residual copy) on the stream.
-int enqueue_window(pkr_ctx* C)
+// Queue one window of a lane (K steps + reduction + residual copy).
+int enqueue_window(pkr_ctx* C, Lane& L)
 {
     for (int k = 0; k < C->K; ++k) {
-        if (launch_batch_step(C->cfg.lattice, C->cfg.precision, C->variant, C->d_state, C->K,
-                              C->grid, C->stream) != 0 ||
-            launch_batch_increment(C->d_state, C->stream) != 0)
+        if (launch_batch_step(C->cfg.lattice, L.prec, L.variant, L.d_state, C->K, L.grid,
+                              C->stream) != 0 ||
+            launch_batch_increment(L.d_state, C->stream) != 0)
             return PKR_ECUDA;
     }
-    if (launch_batch_reduce(C->d_state, C->max_grids, C->grid_stride, C->stream) != 0 ||
-        cudaMemcpyAsync(C->h_res, C->d_res, (size_t)C->max_grids * 3 * sizeof(double),
+    if (launch_batch_reduce(L.d_state, C->max_grids, L.grid_stride, C->stream) != 0 ||
+        cudaMemcpyAsync(L.h_res, L.d_res, (size_t)C->max_grids * 3 * sizeof(double),
                         cudaMemcpyDeviceToHost, C->stream) != cudaSuccess)
         return PKR_ECUDA;
     return PKR_OK;
 }
 
-int run_window(pkr_ctx* C)
+// Launch a lane's window (its captured graph; captured on first use).
+int launch_window(pkr_ctx* C, Lane& L)
 {
-    if (!C->graph) {
+    if (!L.graph) {
         cudaGraph_t g = nullptr;
         bool ok = cudaStreamBeginCapture(C->stream, cudaStreamCaptureModeThreadLocal) ==
                   cudaSuccess;
-        int rc = ok ? enqueue_window(C) : PKR_ECUDA;
+        int rc = ok ? enqueue_window(C, L) : PKR_ECUDA;
         if (ok) ok = cudaStreamEndCapture(C->stream, &g) == cudaSuccess && rc == PKR_OK;
-        if (ok) ok = cudaGraphInstantiate(&C->graph, g, 0) == cudaSuccess;
+        if (ok) ok = cudaGraphInstantiate(&L.graph, g, 0) == cudaSuccess;
         if (g) cudaGraphDestroy(g);
         if (!ok) {
             cudaGetLastError();
-            C->graph = nullptr;
+            L.graph = nullptr;
         }
     }
-    if (C->graph) {
-        if (cudaGraphLaunch(C->graph, C->stream) != cudaSuccess) return PKR_ECUDA;
-    } else if (enqueue_window(C) != PKR_OK) {
-        return PKR_ECUDA;
-    }
-    if (cudaStreamSynchronize(C->stream) != cudaSuccess) return PKR_ECUDA;
-    C->windows += 1;
-    return PKR_OK;
+    if (L.graph) return cudaGraphLaunch(L.graph, C->stream) == cudaSuccess ? PKR_OK : PKR_ECUDA;
+    return enqueue_window(C, L);
 }
 
-// One scheduling round (caller holds the lock): admit, run a window, retire.
-// Returns 1 if work was done, 0 if idle, < 0 on a CUDA error.
-int round(pkr_ctx* C, std::unique_lock<std::mutex>& lk)
+// Retire (or promote) the grids of lane ln whose check at the end of the
+// window just run decided them.  Caller holds the lock.
+int retire(pkr_ctx* C, int ln, long long step0)
 {
-    // admit (first fit, FIFO order) while memory and descriptor slots allow
-    for (auto it = C->queue.begin(); it != C->queue.end();) {
-        Job* j = *it;
-        if ((int)C->live.size() >= C->max_grids) break;
-        if (C->used + job_bytes(C, j->V) > C->budget) {
-            ++it;
-            continue;
-        }
-        int rc = admit(C, j);
-        if (rc == PKR_ENOMEM) {
-            ++it;
-            continue;
-        }
-        it = C->queue.erase(it);
-        if (rc != PKR_OK) {
-            free_job_memory(C, j);
-            finish(C, j, rc);
-            continue;
-        }
-        C->live.push_back(j);
-        C->dirty = true;
-    }
-    if (C->live.empty()) {
-        // nothing runs, so nothing will free memory: a queued request that
-        // could not be allocated now never will be
-        if (!C->queue.empty()) {
-            Job* j = C->queue.front();
-            C->queue.pop_front();
-            finish(C, j, PKR_ENOMEM);
-            return 1;
-        }
-        return 0;
-    }
-    if (C->dirty && rebuild(C) != PKR_OK) return -1;
-    // the window runs without the lock so that submissions and polls proceed
-    lk.unlock();
-    int rc = run_window(C);
-    lk.lock();
-    if (rc != PKR_OK) return -1;
-    const long long step0 = C->step;
-    C->step += C->K;
-    // retire
+    Lane& L = C->lane[ln];
     std::vector<Job*> keep;
     bool changed = false;
-    for (size_t k = 0; k < C->live.size(); ++k) {
-        Job* j = C->live[k];
-        const long long age_end = C->step - 1 - j->join;    // age of the window's last step
-        C->site_updates += (double)j->V * (double)(C->step - (step0 > j->join ? step0 : j->join));
+    for (size_t k = 0; k < L.live.size(); ++k) {
+        Job* j = L.live[k];
+        const long long age_end = L.step - 1 - j->join;    // age of the window's last step
+        C->site_updates += (double)j->V * (double)(L.step - (step0 > j->join ? step0 : j->join));
         const bool checked = age_end >= 1;
-        const double* r = C->h_res + 3 * k;
+        const double* r = L.h_res + 3 * k;
         const double res = r[j->prob.tol_kind == PKR_TOL_MAX_ABS_DPHI ? 0 : 1];
+        const double tol = j->prob.tol;
         int status = PKR_EBUSY;
+        bool move = false;
         if (checked) {
-            if (!std::isfinite(r[0]) || !std::isfinite(r[2])) status = PKR_EDIVERGED;
-            else if (j->prob.tol > 0.0 && res < j->prob.tol) status = PKR_OK;
-            else if (age_end >= j->prob.max_sweeps)
-                status = (j->prob.tol > 0.0) ? PKR_ENOCONV : PKR_OK;
+            if (!std::isfinite(r[0]) || !std::isfinite(r[2])) {
+                status = PKR_EDIVERGED;
+            } else if (C->mixed && ln == 0 && tol > 0.0 && tol < PKR_MIXED_SWITCH_TOL) {
+                // binary32 lane: hand over at the switch tolerance, or once
+                // the residual stops falling (the binary32 rounding floor)
+                if ((res < PKR_MIXED_SWITCH_TOL || (res >= j->prev_res && res < 1e-3)) &&
+                    age_end < j->prob.max_sweeps)
+                    move = true;
+                j->prev_res = res;
+            } else if (tol > 0.0 && res < tol) {
+                status = PKR_OK;
+            }
+            if (status == PKR_EBUSY && !move && age_end >= j->prob.max_sweeps)
+                status = (tol > 0.0) ? PKR_ENOCONV : PKR_OK;
+        }
+        if (move) {
+            const int rc = promote(C, j);
+            if (rc == PKR_OK) {
+                changed = true;
+                continue;
+            }
+            if (rc != PKR_ENOMEM) status = rc;   // else: device memory short, stay in binary32
         }
         if (status == PKR_EBUSY) {
             keep.push_back(j);
@@ -413,9 +501,89 @@ int round(pkr_ctx* C, std::unique_lock<std::mutex>& lk)
         finish(C, j, status);
         changed = true;
     }
-    C->live.swap(keep);
-    if (changed) C->dirty = true;
+    L.live.swap(keep);
+    if (changed) L.dirty = true;
+    return PKR_OK;
+}
+
+// One scheduling round (caller holds the lock): admit, run a window of every
+// lane with live grids, retire/promote.  Returns 1 if work was done, 0 if
+// idle, < 0 on a CUDA error.
+int round(pkr_ctx* C, std::unique_lock<std::mutex>& lk)
+{
+    // admit (first fit, FIFO order) while memory and descriptor slots allow
+    Lane& L0 = C->lane[0];
+    for (auto it = C->queue.begin(); it != C->queue.end();) {
+        Job* j = *it;
+        // descriptor slots: a job lives in one lane at a time, so the lanes
+        // together never hold more than max_grids
+        if ((int)(L0.live.size() + C->lane[1].live.size()) >= C->max_grids) break;
+        if (C->used + job_bytes(C, j->V) > C->budget) {
+            ++it;
+            continue;
+        }
+        int rc = admit(C, j);
+        if (rc == PKR_ENOMEM) {
+            ++it;
+            continue;
+        }
+        it = C->queue.erase(it);
+        if (rc != PKR_OK) {
+            free_job_memory(C, j);
+            finish(C, j, rc);
+            continue;
+        }
+        L0.live.push_back(j);
+        L0.dirty = true;
+    }
+    bool any = false;
+    for (int ln = 0; ln < C->nlanes; ++ln) any = any || !C->lane[ln].live.empty();
+    if (!any) {
+        // nothing runs, so nothing will free memory: a queued request that
+        // could not be allocated now never will be
+        if (!C->queue.empty()) {
+            Job* j = C->queue.front();
+            C->queue.pop_front();
+            finish(C, j, PKR_ENOMEM);
+            return 1;
+        }
+        return 0;
+    }
+    bool ran[2] = {false, false};
+    for (int ln = 0; ln < C->nlanes; ++ln) {
+        Lane& L = C->lane[ln];
+        if (L.live.empty()) continue;
+        if (L.dirty && rebuild(C, L) != PKR_OK) return -1;
+        ran[ln] = true;
+    }
+    // the windows run without the lock so that submissions and polls proceed
+    lk.unlock();
+    int rc = PKR_OK;
+    for (int ln = 0; ln < C->nlanes && rc == PKR_OK; ++ln)
+        if (ran[ln]) rc = launch_window(C, C->lane[ln]);
+    if (rc == PKR_OK && cudaStreamSynchronize(C->stream) != cudaSuccess) rc = PKR_ECUDA;
+    lk.lock();
+    if (rc != PKR_OK) return -1;
+    // binary64 lane first, so that grids promoted in this round wait for the next window
+    for (int ln = C->nlanes - 1; ln >= 0; --ln) {
+        if (!ran[ln]) continue;
+        Lane& L = C->lane[ln];
+        const long long step0 = L.step;
+        L.step += C->K;
+        C->windows += 1;
+        retire(C, ln, step0);
+    }
     return 1;
+}
+
+void fail_all(pkr_ctx* C)
+{
+    for (int ln = 0; ln < C->nlanes; ++ln) {
+        for (Job* j : C->lane[ln].live) finish(C, j, PKR_ECUDA);
+        C->lane[ln].live.clear();
+    }
+    for (Job* j : C->queue) finish(C, j, PKR_ECUDA);
+    C->queue.clear();
 }
 
 void worker_main(pkr_ctx* C)
@@ -426,17 +594,43 @@ void worker_main(pkr_ctx* C)
         int r = round(C, lk);
         if (r < 0) {
             // a CUDA error: fail everything that is queued or live
-            for (Job* j : C->live) finish(C, j, PKR_ECUDA);
-            for (Job* j : C->queue) finish(C, j, PKR_ECUDA);
-            C->live.clear();
-            C->queue.clear();
+            fail_all(C);
             continue;
         }
         if (r == 0) C->cv_work.wait(lk, [&] { return C->stop || !C->queue.empty(); });
     }
 }
 
-int tune_variant(pkr_ctx* C, int edge);
+int tune_variant(pkr_ctx* C, Lane& L, int edge);
+
+bool init_lane(pkr_ctx* C, Lane& L, int prec)
+{
+    L.prec = prec;
+    L.elem = prec == PKR_FP64 ? 8 : 4;
+    L.grid_stride = prec == PKR_FP64 ? (int)sizeof(BatchGrid<double>)
+                                     : (int)sizeof(BatchGrid<float>);
+    L.h_grids.assign((size_t)C->max_grids * L.grid_stride, 0);
+    std::memset(&L.h_state, 0, sizeof(BatchState));
+    return cudaMalloc((void**)&L.d_state, sizeof(BatchState)) == cudaSuccess &&
+           cudaMalloc((void**)&L.d_grids, (size_t)C->max_grids * L.grid_stride) == cudaSuccess &&
+           cudaMalloc((void**)&L.d_res, (size_t)C->max_grids * 3 * sizeof(double)) ==
+               cudaSuccess &&
+           cudaMallocHost((void**)&L.h_res, (size_t)C->max_grids * 3 * sizeof(double)) ==
+               cudaSuccess &&
+           cudaMemcpy(L.d_state, &L.h_state, sizeof(BatchState), cudaMemcpyHostToDevice) ==
+               cudaSuccess;
+}
+
+void free_lane(Lane& L)
+{
+    if (L.graph) cudaGraphExecDestroy(L.graph);
+    cudaFree(L.d_state);
+    cudaFree(L.d_grids);
+    cudaFree(L.d_res);
+    if (L.d_tile_partials) cudaFree(L.d_tile_partials);
+    if (L.h_res) cudaFreeHost(L.h_res);
+    L = Lane();
+}
 
 }  // namespace
 
@@ -447,70 +641,59 @@ int pkr_ctx_create(const pkr_ctx_config* cfg, void* stream, pkr_ctx** out)
     if (!cfg || !out) return PKR_EINVAL;
     *out = nullptr;
     if (cfg->check_every < 1 || cfg->hbm_budget_bytes == 0) return PKR_EINVAL;
-    if (cfg->precision != PKR_FP64 && cfg->precision != PKR_FP32) return PKR_EINVAL;
+    if (cfg->precision != PKR_FP64 && cfg->precision != PKR_FP32 &&
+        cfg->precision != PKR_MIXED)
+        return PKR_EINVAL;
     LatticeInfo li;
     int rc = build_lattice(cfg->lattice, cfg->order, &li);
     if (rc != PKR_OK) return rc;
+    const int nvar = pkr_variant_count(cfg->lattice);
+    if (cfg->variant >= nvar || cfg->variant < -2) return PKR_EINVAL;
     pkr_ctx* C = new (std::nothrow) pkr_ctx();
     if (!C) return PKR_ENOMEM;
     C->cfg = *cfg;
     C->li = li;
     C->stream = (cudaStream_t)stream;
-    C->elem = cfg->precision == PKR_FP64 ? 8 : 4;
     C->K = cfg->check_every;
     C->budget = cfg->hbm_budget_bytes;
     C->max_grids = cfg->max_grids > 0 ? cfg->max_grids : 4096;
-    C->grid_stride = cfg->precision == PKR_FP64 ? (int)sizeof(BatchGrid<double>)
-                                                : (int)sizeof(BatchGrid<float>);
-    C->h_grids.assign((size_t)C->max_grids * C->grid_stride, 0);
+    C->mixed = cfg->precision == PKR_MIXED;
+    C->nlanes = C->mixed ? 2 : 1;
     bool ok = cudaGetDevice(&C->device) == cudaSuccess &&
               cudaDeviceGetAttribute(&C->nsm, cudaDevAttrMultiProcessorCount, C->device) ==
-                  cudaSuccess &&
-              cudaMalloc((void**)&C->d_state, sizeof(BatchState)) == cudaSuccess &&
-              cudaMalloc((void**)&C->d_grids, (size_t)C->max_grids * C->grid_stride) ==
-                  cudaSuccess &&
-              cudaMalloc((void**)&C->d_res, (size_t)C->max_grids * 3 * sizeof(double)) ==
                   cudaSuccess &&
               cudaMalloc((void**)&C->d_scratch, kScratchBlocks * sizeof(double)) == cudaSuccess &&
               cudaMalloc((void**)&C->d_flag, sizeof(int)) == cudaSuccess &&
               cudaMalloc((void**)&C->d_mean, sizeof(double)) == cudaSuccess &&
-              cudaMallocHost((void**)&C->h_res, (size_t)C->max_grids * 3 * sizeof(double)) ==
-                  cudaSuccess &&
               cudaMallocHost((void**)&C->h_flag, sizeof(int)) == cudaSuccess &&
               cudaMallocHost((void**)&C->h_mean, sizeof(double)) == cudaSuccess;
+    const int precs[2] = {C->mixed ? PKR_FP32 : cfg->precision, PKR_FP64};
+    for (int ln = 0; ok && ln < C->nlanes; ++ln) ok = init_lane(C, C->lane[ln], precs[ln]);
     if (!ok) {
         cudaGetLastError();
         pkr_ctx_destroy(C);
         return PKR_ENOMEM;
     }
-    std::memset(&C->h_state, 0, sizeof(BatchState));
-    if (cudaMemcpy(C->d_state, &C->h_state, sizeof(BatchState), cudaMemcpyHostToDevice) !=
-        cudaSuccess) {
-        pkr_ctx_destroy(C);
-        return PKR_ECUDA;
-    }
-    const int nvar = pkr_variant_count(cfg->lattice);
-    int var = cfg->variant;
-    if (var >= nvar || var < -2) {
-        pkr_ctx_destroy(C);
-        return PKR_EINVAL;
-    }
-    if (var == -2) {
-        var = tune_variant(C, cfg->probe_edge > 0 ? cfg->probe_edge : 64);
-        if (var < 0) {
+    for (int ln = 0; ln < C->nlanes; ++ln) {
+        Lane& L = C->lane[ln];
+        int var = cfg->variant;
+        if (var == -2) {
+            var = tune_variant(C, L, cfg->probe_edge > 0 ? cfg->probe_edge : 64);
+            if (var < 0) {
+                pkr_ctx_destroy(C);
+                return PKR_ECUDA;
+            }
+        } else if (var == -1) {
+            var = nvar > 2 ? 2 : 0;
+        }
+        L.variant = var;
+        int bps = 0;
+        if (batch_occupancy(cfg->lattice, L.prec, var, &bps) != 0 || bps < 1) {
             pkr_ctx_destroy(C);
             return PKR_ECUDA;
         }
-    } else if (var == -1) {
-        var = nvar > 2 ? 2 : 0;
+        L.grid = C->nsm * bps;
     }
-    C->variant = var;
-    int bps = 0;
-    if (batch_occupancy(cfg->lattice, cfg->precision, var, &bps) != 0 || bps < 1) {
-        pkr_ctx_destroy(C);
-        return PKR_ECUDA;
-    }
-    C->grid = C->nsm * bps;
     if (cfg->threaded) C->worker = std::thread(worker_main, C);
     *out = C;
     return PKR_OK;
@@ -582,7 +765,10 @@ int pkr_ctx_wait(pkr_ctx* C, uint64_t ticket, pkr_stats* st)
     if (!C->cfg.threaded) {
         while (j->status == PKR_EBUSY) {
             int r = round(C, lk);
-            if (r < 0) return PKR_ECUDA;
+            if (r < 0) {
+                fail_all(C);
+                return PKR_ECUDA;
+            }
             if (r == 0 && j->status == PKR_EBUSY) return PKR_EINVAL;
         }
     } else {
@@ -599,7 +785,10 @@ int pkr_ctx_run(pkr_ctx* C, int64_t max_windows)
     int64_t n = 0;
     while (max_windows <= 0 || n < max_windows) {
         int r = round(C, lk);
-        if (r < 0) return PKR_ECUDA;
+        if (r < 0) {
+            fail_all(C);
+            return PKR_ECUDA;
+        }
         if (r == 0) break;
         ++n;
     }
@@ -615,7 +804,7 @@ int pkr_ctx_info(pkr_ctx* C, int64_t* finished, double* site_updates, int64_t* w
     if (site_updates) *site_updates = C->site_updates;
     if (windows) *windows = C->windows;
     if (bytes_in_use) *bytes_in_use = C->used;
-    if (variant) *variant = C->variant;
+    if (variant) *variant = C->lane[0].variant;
     return PKR_OK;
 }
 
@@ -629,7 +818,7 @@ int pkr_ctx_destroy(pkr_ctx* C)
     C->cv_work.notify_all();
     C->cv_done.notify_all();
     if (C->worker.joinable()) C->worker.join();
-    if (C->stream || C->d_state) cudaStreamSynchronize(C->stream);
+    if (C->stream || C->lane[0].d_state) cudaStreamSynchronize(C->stream);
     for (auto& kv : C->jobs) {
         Job* j = kv.second;
         for (int k = 0; k < 2; ++k)
@@ -638,15 +827,10 @@ int pkr_ctx_destroy(pkr_ctx* C)
         if (j->Phi) cudaFree(j->Phi);
         delete j;
     }
-    if (C->graph) cudaGraphExecDestroy(C->graph);
-    cudaFree(C->d_state);
-    cudaFree(C->d_grids);
-    cudaFree(C->d_res);
+    for (int ln = 0; ln < 2; ++ln) free_lane(C->lane[ln]);
     cudaFree(C->d_scratch);
     cudaFree(C->d_flag);
     cudaFree(C->d_mean);
-    if (C->d_tile_partials) cudaFree(C->d_tile_partials);
-    if (C->h_res) cudaFreeHost(C->h_res);
     if (C->h_flag) cudaFreeHost(C->h_flag);
     if (C->h_mean) cudaFreeHost(C->h_mean);
     delete C;
@@ -657,11 +841,11 @@ int pkr_ctx_destroy(pkr_ctx* C)
 
 namespace {
 
-// Autotuner of the batch geometry: time one step of every compiled variant on
-// a probe grid (edge^3, zero source) in this context's batch layout, keep
-// the fastest.  Runs at context creation, before any request, so that every
-// request of the context sees the same kernel.
-int tune_variant(pkr_ctx* C, int edge)
+// Autotuner of a lane's batch geometry: time three steps of every compiled
+// variant on a probe grid (edge^3, zero source) in the lane's batch layout,
+// keep the fastest.  Runs at context creation, before any request, so that
+// every request of the context sees the same kernels.
+int tune_variant(pkr_ctx* C, Lane& L, int edge)
 {
     const int nvar = pkr_variant_count(C->cfg.lattice);
     Job probe;
@@ -673,10 +857,10 @@ int tune_variant(pkr_ctx* C, int edge)
     probe.omega = 0.5;
     for (int k = 0; k < C->li.dim; ++k)
         if (probe.prob.n[k] < C->li.reach) probe.small = 1;
-    const size_t popb = (size_t)C->li.Q * (size_t)probe.V * (size_t)C->elem;
+    const size_t popb = (size_t)C->li.Q * (size_t)probe.V * (size_t)L.elem;
     if (cudaMalloc(&probe.pop[0], popb) != cudaSuccess ||
         cudaMalloc(&probe.pop[1], popb) != cudaSuccess ||
-        cudaMalloc(&probe.S, (size_t)probe.V * C->elem) != cudaSuccess ||
+        cudaMalloc(&probe.S, (size_t)probe.V * L.elem) != cudaSuccess ||
         cudaMalloc((void**)&probe.Phi, (size_t)probe.V * 8) != cudaSuccess) {
         cudaGetLastError();
         for (int k = 0; k < 2; ++k) cudaFree(probe.pop[k]);
@@ -686,26 +870,24 @@ int tune_variant(pkr_ctx* C, int edge)
     }
     cudaMemset(probe.pop[0], 0, popb);
     cudaMemset(probe.pop[1], 0, popb);
-    cudaMemset(probe.S, 0, (size_t)probe.V * C->elem);
+    cudaMemset(probe.S, 0, (size_t)probe.V * L.elem);
     probe.join = -1;   // never the zero-in step: the timed steps pull real data
-    C->live.push_back(&probe);
+    L.live.push_back(&probe);
     int best = -1;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    if (rebuild(C) == PKR_OK) {
+    if (rebuild(C, L) == PKR_OK) {
         for (int v = 0; v < nvar; ++v) {
             int bps = 0;
-            if (batch_occupancy(C->cfg.lattice, C->cfg.precision, v, &bps) != 0 || bps < 1)
-                continue;
+            if (batch_occupancy(C->cfg.lattice, L.prec, v, &bps) != 0 || bps < 1) continue;
             const int grid = C->nsm * bps;
-            launch_batch_step(C->cfg.lattice, C->cfg.precision, v, C->d_state, 1 << 30, grid,
-                              C->stream);
+            launch_batch_step(C->cfg.lattice, L.prec, v, L.d_state, 1 << 30, grid, C->stream);
             cudaEventRecord(e0, C->stream);
             for (int k = 0; k < 3; ++k)
-                launch_batch_step(C->cfg.lattice, C->cfg.precision, v, C->d_state, 1 << 30,
-                                  grid, C->stream);
+                launch_batch_step(C->cfg.lattice, L.prec, v, L.d_state, 1 << 30, grid,
+                                  C->stream);
             cudaEventRecord(e1, C->stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) break;
             float ms = 0.f;
@@ -718,11 +900,11 @@ int tune_variant(pkr_ctx* C, int edge)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    C->live.clear();
-    C->dirty = true;
-    C->step = 0;
-    std::memset(&C->h_state, 0, sizeof(BatchState));
-    cudaMemcpy(C->d_state, &C->h_state, sizeof(BatchState), cudaMemcpyHostToDevice);
+    L.live.clear();
+    L.dirty = true;
+    L.step = 0;
+    std::memset(&L.h_state, 0, sizeof(BatchState));
+    cudaMemcpy(L.d_state, &L.h_state, sizeof(BatchState), cudaMemcpyHostToDevice);
     for (int k = 0; k < 2; ++k) cudaFree(probe.pop[k]);
     cudaFree(probe.S);
     cudaFree(probe.Phi);

@@ -169,5 +169,7 @@ def test_context_config_validation(pk_cfg=None):
     assert create(check_every=0) == -1
     assert create(hbm_budget_bytes=0) == -1
     assert create(precision=7) == -1
+    assert create(precision=3) == -1      # binary16 storage: pkr_solve only
+    assert create(variant=99) == -1
     assert create(order=7) == -1
     assert create(lattice=42) == -1

@@ -137,3 +137,58 @@ def test_autotuned_context_and_errors(pk):
     with pytest.raises(pk.PkrError):          # unstable relaxation time
         ctx.submit(r, torch.zeros_like(r), tau_lb=0.6, tol=1e-6)
     ctx.close()
+
+
+def _fixed_point(pk, rho, tau):
+    import torch
+    r = torch.from_numpy(np.ascontiguousarray(rho)).cuda()
+    fx = torch.empty_like(r)
+    pk.fixed_point_fft(r, fx, pk.problem("D3Q111", rho.shape, 5, tau_lb=tau))
+    return fx.cpu().numpy()
+
+
+MIXED_JOBS = [((12, 10, 14), 1.3, 1e-10, 4), ((9, 7, 13), 2.0, 1e-9, 5),
+              ((16, 16, 16), 1.1, 1e-11, 6), ((2, 3, 5), 1.4, 1e-9, 7),
+              ((20, 11, 8), 3.0, 1e-6, 8)]
+
+
+@pytest.mark.parametrize("threaded", [False, True])
+def test_mixed_batch_reaches_binary64_tolerances(pk, threaded):
+    """MIXED context: every request meets its tolerance (below what binary32
+    can reach for all but the last), and lands as close to the scheme's exact
+    fixed point as that tolerance allows (error ~ residual / spectral gap;
+    the gap of these grids is >= 0.05, so 50 x tol bounds it, plus the
+    binary32 floor for the request that finishes in binary32)."""
+    res, info = _run_ctx(pk, MIXED_JOBS, "mixed", threaded=threaded)
+    assert info["finished"] == len(MIXED_JOBS) and info["bytes_in_use"] == 0
+    for rho, got, rc, st, tau, tol in res:
+        assert rc == 0, rc
+        assert st["residual"] < tol
+        assert (st["sweeps"] + 1) % 8 == 0
+        fx = _fixed_point(pk, rho, tau)
+        assert _rel(got, fx) <= 50 * tol + (2e-5 if tol >= 1e-6 else 0.0), (rho.shape, _rel(got, fx))
+
+
+def test_mixed_same_result_alone_and_in_mix(pk):
+    alone, _ = _run_ctx(pk, MIXED_JOBS[:1], "mixed")
+    mixed, _ = _run_ctx(pk, MIXED_JOBS[1:3] + MIXED_JOBS[:1] + MIXED_JOBS[3:], "mixed")
+    a, b = alone[0], mixed[2]
+    assert a[3]["sweeps"] == b[3]["sweeps"]
+    assert np.array_equal(a[1], b[1])
+
+
+def test_mixed_budget_reserves_both_states(pk):
+    """A MIXED request reserves its binary32 and binary64 states and Phi; a
+    budget of 1.5 such reservations runs the requests one at a time, with
+    the same results as with room for all."""
+    shape = (16, 16, 16)
+    V = 16 ** 3
+    one = 2 * 111 * V * 4 + V * 4 + 2 * 111 * V * 8 + V * 8 + V * 8
+    jobs = [(shape, 1.3, 1e-9, s) for s in (11, 12, 13)]
+    tight, info = _run_ctx(pk, jobs, "mixed", budget=int(1.5 * one))
+    roomy, _ = _run_ctx(pk, jobs, "mixed", budget=10 ** 9)
+    for a, b in zip(tight, roomy):
+        assert a[2] == 0 and np.array_equal(a[1], b[1])
+    with pytest.raises(pk.PkrError) as e:
+        _run_ctx(pk, jobs[:1], "mixed", budget=one - 1)
+    assert e.value.status == -2
