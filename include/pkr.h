@@ -82,10 +82,11 @@ typedef enum pkr_lattice {
  * passes 2^54).  The density is an exact integer sum and the relaxation a
  * 64 x 64-bit fixed-point product by (1 - omega) (rounded to nearest) plus
  * the per-class equilibrium-and-source term; only that term and the density
- * conversion use binary64.  Every value keeps >= 54 significant bits relative
- * to the largest stored value, as accurate as binary64 for the field as a
- * whole.  On GPUs with little binary64 throughput it runs the sweep on the
- * integer units. */
+ * conversion use binary64.  The largest stored value stays in [2^51, 2^54],
+ * so every value is resolved to 2^-51 or finer relative to the largest one:
+ * about binary64's accuracy for the field as a whole (not for values many
+ * orders below the largest).  On GPUs with little binary64 throughput it runs
+ * the sweep on the integer units. */
 typedef enum pkr_precision {
     PKR_FP64 = 0, PKR_FP32 = 1, PKR_MIXED = 2, PKR_FP16 = 3, PKR_MIXED16 = 4, PKR_FX64 = 5
 } pkr_precision;

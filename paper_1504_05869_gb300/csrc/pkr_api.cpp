@@ -153,7 +153,8 @@ struct pkr_plan {
     unsigned int* h16max;  // binary16 storage: max |p| of the current step
     int* h16of;            // binary16 storage: overflow flag
     int* fxF;              // fixed-point storage: exponents of the two arrays
-    unsigned long long* fxmax;  // fixed-point storage: max |stored| of the current step
+    unsigned long long* fxmax;  // fixed-point storage: OR of |stored| over the current step
+                                // (its bit length is that of the largest |stored|)
     long long cfx;         // fixed-point storage: round((1 - omega) 2^62)
     bool loaded;
     Coefs<double> c64;

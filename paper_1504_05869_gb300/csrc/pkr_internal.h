@@ -89,7 +89,8 @@ struct SweepArgs {
     unsigned int* pmax;
     int* oflow;
     // 64-bit fixed-point storage only: exponents fxF[2] (a value v is stored
-    // as round(v 2^fxF[k]) in array k), max |stored| of this step, and
+    // as round(v 2^fxF[k]) in array k), the OR of |stored| over this step
+    // (bit length of the largest |stored|), and
     // 1 - omega as round((1 - omega) 2^62)
     int* fxF;
     unsigned long long* fxmax;
@@ -122,7 +123,8 @@ int launch_convert_shift(const void* in, int in_precision, void* out, int out_pr
 // writes (sc[next]) from this step's max |p| (4x headroom), reset the max.
 int launch_h16_rescale(float* sc, unsigned int* pmax, int next, void* stream);
 // 64-bit fixed-point storage: after a step, set the exponent of the array the
-// next step writes from this step's max |stored| (keep it below 2^54), reset.
+// next step writes from the bit length of this step's largest |stored| (the
+// OR of all of them; keep it below 2^54), reset.
 int launch_fx_rescale(int* F, unsigned long long* fmax, int next, void* stream);
 // max |S| of a binary64 source as bits (atomicMax into *out).
 int launch_absmax_f64(const double* S, int64_t V, unsigned long long* out, void* stream);

@@ -286,12 +286,11 @@ __device__ __forceinline__ long long lds_s64(uint32_t addr)
     return v;
 }
 
-// round(q c / 2^(62 + sh)) for the fixed-point relaxation (c = (1 - omega) 2^62)
-__device__ __forceinline__ long long fx_mul(long long q, long long c, int sh)
+// round(q c / 2^62), rounding half up (c = (1 - omega) 2^62 for the relaxation)
+__device__ __forceinline__ long long fx_mul(long long q, long long c)
 {
-    const int s = 62 + sh;
-    const __int128 prod = (__int128)q * (__int128)c + ((__int128)1 << (s - 1));
-    return (long long)(prod >> s);
+    const __int128 prod = (__int128)q * (__int128)c + ((__int128)1 << 61);
+    return (long long)(prod >> 62);
 }
 
 // 2^e as a binary64 (|e| < 1000)
@@ -443,13 +442,15 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
                 if constexpr (i0 < i1 && std::is_same<T, long long>::value) {
                     const double e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
                     const long long ei = __double2ll_rn(e * pow2(tg.fw));
-                    const int sh = tg.fr - tg.fw;
+                    // the written array's scale is 2^-k that of the read one (k >= 0,
+                    // the rescale only lowers it): fold 2^-k into the coefficient
+                    const int k = tg.fr - tg.fw;
+                    const long long cw = k == 0 ? tg.cfx : ((tg.cfx >> (k - 1)) + 1) >> 1;
                     T* dst = B + ((int64_t)i0 * V + s);
 #pragma unroll 4
                     for (int i = i0; i < i1; ++i) {
-                        const long long p = fx_mul(lds_s64(sbase + (i - lo) * 256), tg.cfx, sh) + ei;
-                        const unsigned long long ap = (unsigned long long)(p < 0 ? -p : p);
-                        fxm = ap > fxm ? ap : fxm;
+                        const long long p = fx_mul(lds_s64(sbase + (i - lo) * 256), cw) + ei;
+                        fxm |= (unsigned long long)(p ^ (p >> 63));
                         store_stream(dst, (T)p);
                         dst += V;
                     }
@@ -525,10 +526,9 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     if constexpr (std::is_same<T, long long>::value) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long v = __shfl_down_sync(0xffffffffu, fxm, o);
-            fxm = v > fxm ? v : fxm;
+            fxm |= __shfl_down_sync(0xffffffffu, fxm, o);
         }
-        if (lane == 0 && fxm) atomicMax(a.fxmax, fxm);
+        if (lane == 0 && fxm) atomicOr(a.fxmax, fxm);
     }
 
     if (a.mode == kCheck) {
