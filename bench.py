@@ -513,7 +513,7 @@ def run_precision(args):
         rho, _ = stiff_source((512, 512, 512), count=256, sigma=1.5, seed=1)
         r = torch.from_numpy(rho).cuda()
         del rho
-        for prec in ("fp16", "fp32", "fp64"):
+        for prec in ("fp16", "fp32", "fp64", "fx64"):
             stream = torch.cuda.Stream()
             prob = pk.problem("D3Q111", r.shape, 5, knudsen=KN, max_sweeps=10 ** 6,
                               precision=prec)
@@ -527,12 +527,37 @@ def run_precision(args):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / 8
-            es = {"fp64": 8, "fp32": 4, "fp16": 2}[prec]
-            ss = 8 if prec == "fp64" else 4
+            es = {"fp64": 8, "fx64": 8, "fp32": 4, "fp16": 2}[prec]
+            ss = 8 if prec in ("fp64", "fx64") else 4
             out["throughput_512"][prec] = {"ms_per_sweep": ms, "glups": r.numel() / ms / 1e6,
                                            "gbs": r.numel() * (2 * 111 * es + ss) / ms / 1e6,
                                            "bytes_per_site": 2 * 111 * es + ss}
             torch.cuda.empty_cache()
+        if args.solve_512:
+            # each storage solved to its tolerance at 512^3, against the exact
+            # binary64 fixed point (the mixed ladders are left out here: they
+            # hold the binary32 and binary64 states at once, 357 GB at 512^3)
+            ref = torch.empty_like(r)
+            prob = pk.problem("D3Q111", r.shape, 5, knudsen=KN)
+            fst = pk.fixed_point_fft(r, ref, prob)
+            nref = torch.linalg.norm(ref).item()
+            out["solve_512"] = {"fixed_point_seconds": fst["wall_ms"] / 1e3}
+            for prec, tol in (("fp16", 1e-3), ("fp32", 1e-7), ("fp64", 1e-10)):
+                phi = torch.empty_like(r)
+                prob = pk.problem("D3Q111", r.shape, 5, knudsen=KN, tol=tol, tol_kind="rel_l2",
+                                  check_every=SWEEPS_PER_STEP, max_sweeps=200000,
+                                  precision=prec)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, st = pk.solve(r, phi, prob)
+                torch.cuda.synchronize()
+                out["solve_512"][prec] = {
+                    "seconds": time.perf_counter() - t0, "sweeps": st["sweeps"], "status": rc,
+                    "tol": tol, "rel_l2_vs_fp64_fixed_point":
+                        torch.linalg.norm(phi - ref).item() / nref}
+                del phi
+                torch.cuda.empty_cache()
+            del ref
         del r
         torch.cuda.empty_cache()
     rho, _ = stiff_source(SHAPE, count=64, sigma=2.0, seed=0)
@@ -560,7 +585,8 @@ def run_precision(args):
                         "seconds": time.perf_counter() - t0, "library_wall_ms": st["wall_ms"]}
     nref = torch.linalg.norm(ref).item()
     for label, prec, tol in (("fp64", "fp64", args.target_tol), ("mixed", "mixed", args.target_tol),
-                             ("mixed16", "mixed16", args.target_tol), ("fp32", "fp32", 1e-7),
+                             ("mixed16", "mixed16", args.target_tol),
+                             ("fx64", "fx64", args.target_tol), ("fp32", "fp32", 1e-7),
                              ("fp16", "fp16", 1e-3)):
         phi, rc, st, dt = solve(prec, tol)
         err = (torch.linalg.norm(phi - ref).item() / nref)
@@ -703,6 +729,8 @@ def main():
                     choices=["sweep", "batch", "serve", "poisson2d", "precision", "tau1",
                              "knudsen"])
     ap.add_argument("--no-512", action="store_true")
+    ap.add_argument("--solve-512", action="store_true",
+                    help="precision workload: also solve at 512^3 against the FFT fixed point")
     ap.add_argument("--target-tol", type=float, default=1e-10)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--requests", type=int, default=48)
