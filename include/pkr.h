@@ -111,8 +111,11 @@ typedef struct pkr_problem {
     int32_t check_every;  /* steps between residual checks (<= 0: 32) */
     int64_t max_sweeps;   /* upper bound on the steps taken (>= 1) */
     int32_t variant;      /* sweep kernel geometry: -1 = library default, 0 .. count-1 =
-                             a compiled variant (pkr_variant_count); all variants give
-                             identical results, they differ only in speed.  With -1, a
+                             a compiled variant (pkr_variant_count); in binary64 and
+                             fixed point all variants give identical results (binary32
+                             ones differ in rounding), they differ in speed.  -1 picks
+                             a geometry by grid size (more warps per tile on grids of
+                             a few tiles per SM).  With -1, a
                              binary64 problem at tau_lb == 1 (omega = 1, the paper's
                              setting) runs as the scalar stencil Phi' = sum_i phi_i
                              Phi(x - v_i) + sum_i chi_i S(x - v_i): at omega = 1 the
@@ -187,7 +190,12 @@ int pkr_plan_load_source(pkr_plan *plan, const double *rho, int rho_on_host);
 /* Advance until Phi^(t + steps) is known, checking the residual every
  * check_every steps (<= 0: the problem's value) and stopping early once it
  * drops below tol (tol <= 0: never).  stats may be NULL.  Returns PKR_OK,
- * PKR_EDIVERGED or PKR_ECUDA.  Synchronises once per check. */
+ * PKR_EDIVERGED or PKR_ECUDA.  Synchronises once per check; except that a
+ * binary64 run that checks every step (check_every = 1, tol > 0, steps >= 64)
+ * runs its steps as a CUDA graph of 64 steps captured on a stream of the plan
+ * and launched on the plan's stream, with the stopping rule applied on the
+ * device after each check: same steps and stopping step, one synchronisation
+ * per 64 steps. */
 int pkr_plan_run(pkr_plan *plan, int64_t steps, double tol, int tol_kind, int check_every,
                  pkr_stats *stats);
 

@@ -23,7 +23,7 @@ template <class L> int launch_sweep_h16(const SweepArgs&, const void*, int, void
 template <class L> int occupancy_h16(int*, int*);
 template <class L>
 int launch_stencil(const double*, double*, const double*, const Coefs<double>&, int64_t, int, int,
-                   int, int, int, double*, int, void*);
+                   int, int, int, double*, int, void*, const int*);
 }  // namespace pkr
 
 #define PKR_CK(call)                                     \
@@ -71,10 +71,14 @@ int variant_count(int lattice)
 // D3Q19: the two variants within 0.2 %).  Index into the lattice's variant
 // list {(G,TILES)} = {(1,2),(2,1),(2,2),(3,1),(3,2),(4,1)} for Q > 64, else
 // {(1,2),(1,4)}.
-int default_variant(int lattice, int precision)
+// Default geometry: 2 velocity groups x 2 tiles for the large sets; on grids
+// with few tiles per SM, 4 groups x 1 tile (more warps share each tile, so
+// each step's chain is shorter).  All geometries give the same binary64 result.
+int default_variant(int lattice, int precision, int64_t V, int nsm)
 {
     (void)precision;
-    return variant_count(lattice) > 2 ? 2 : 0;
+    if (variant_count(lattice) <= 2) return 0;
+    return (V + 31) / 32 <= (int64_t)4 * nsm ? 5 : 2;
 }
 
 int elem_bytes(int precision)
@@ -156,12 +160,33 @@ struct pkr_plan {
     unsigned long long* fxmax;  // fixed-point storage: OR of |stored| over the current step
                                 // (its bit length is that of the largest |stored|)
     long long cfx;         // fixed-point storage: round((1 - omega) 2^62)
+    // device-side stopping (binary64 runs that check every step): a captured
+    // graph of kGraphSteps check steps, each followed by the stopping rule on
+    // the device; steps after a stop return at once (SweepArgs::stop)
+    RunCtl* ctl;           // device state of the rule
+    RunCtl* hctl;          // pinned host copy
+    cudaGraphExec_t gexec; // the captured steps (nullptr: none yet)
+    cudaStream_t cap;      // stream the graph is captured on
+    int gcur, gkind, gj;   // array parity and tol kind the graph was captured for;
+                           // index of the step being captured
+    double gtol;           // tolerance it was captured for
+    const int* stop_arg;   // &ctl->stop while capturing, else nullptr
     bool loaded;
     Coefs<double> c64;
     Coefs<float> c32;
 };
 
 namespace {
+
+// Residual of a check step: plain, or with the device-side stopping rule
+// while the steps of a run are being captured.
+int finalize_step(pkr_plan* P)
+{
+    if (P->stop_arg)
+        return launch_finalize_check(P->partials, P->grid, P->scal + 1, P->ctl, P->gtol, P->gkind,
+                                     P->gj, P->stream);
+    return launch_finalize_residual(P->partials, P->grid, P->scal + 1, P->stream);
+}
 
 int launch_stencil_step(pkr_plan* P, const double* in, double* out, const double* add,
                         const Coefs<double>& c, int check)
@@ -170,7 +195,7 @@ int launch_stencil_step(pkr_plan* P, const double* in, double* out, const double
     const int nx = (int)n[0], ny = (int)n[1], nz = (int)n[2];
     int rc = 0;
 #define PKR_ST(LL) launch_stencil<LL>(in, out, add, c, P->V, nx, ny, nz, P->small, check, \
-                                      P->partials, P->grid, P->stream)
+                                      P->partials, P->grid, P->stream, P->stop_arg)
     switch (P->prob.lattice) {
     case PKR_D1Q5: rc = PKR_ST(D1Q5); break;
     case PKR_D1Q9: rc = PKR_ST(D1Q9); break;
@@ -195,9 +220,7 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
             int rc = launch_stencil_step(P, P->Ps[P->cur], P->Ps[P->cur ^ 1], P->St, P->c64,
                                          check);
             if (rc != PKR_OK) return rc;
-            if (check &&
-                launch_finalize_residual(P->partials, P->grid, P->scal + 1, P->stream) != 0)
-                return PKR_ECUDA;
+            if (check && finalize_step(P) != 0) return PKR_ECUDA;
             P->cur ^= 1;
         }
         P->Phi = P->Ps[P->cur];
@@ -231,6 +254,7 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
     a.sc = P->h16sc;
     a.pmax = P->h16max;
     a.oflow = P->h16of;
+    a.stop = P->stop_arg;
     if (pr == PKR_FP16) {
         switch (P->prob.lattice) {
         case PKR_D1Q5: rc = launch_sweep_h16<D1Q5>(a, c, P->grid, P->stream); break;
@@ -271,8 +295,7 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
     P->cur ^= 1;
     P->launches += 1;
     if (mode == kCheck) {
-        if (launch_finalize_residual(P->partials, P->grid, P->scal + 1, P->stream) != 0)
-            return PKR_ECUDA;
+        if (finalize_step(P) != 0) return PKR_ECUDA;
     }
     return PKR_OK;
 }
@@ -319,6 +342,73 @@ int set_variant(pkr_plan* P, int variant)
     if (grid > kMaxGridBlocks) grid = kMaxGridBlocks;
     P->variant = variant;
     P->grid = (int)grid;
+    if (P->gexec) {   // captured with the previous geometry
+        cudaGraphExecDestroy(P->gexec);
+        P->gexec = nullptr;
+    }
+    return PKR_OK;
+}
+
+// Steps per captured graph of device-stopped check steps (even, so that the
+// arrays are back at the same parity after a full replay).
+constexpr int kGraphSteps = 64;
+
+// Capture kGraphSteps check steps, each followed by the stopping rule on the
+// device, as one graph for this plan, array parity, tol and tol kind.  The
+// host view that launch_one advances (parity, step count, Phi) is restored
+// afterwards: capturing runs nothing.  On failure the caller steps on the host.
+int capture_steps(pkr_plan* P, double tol, int tol_kind)
+{
+    if (!P->ctl) {
+        if (cudaMalloc((void**)&P->ctl, sizeof(RunCtl)) != cudaSuccess ||
+            cudaMallocHost((void**)&P->hctl, sizeof(RunCtl)) != cudaSuccess) {
+            cudaGetLastError();
+            return PKR_ENOMEM;
+        }
+    }
+    if (!P->cap && cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        P->cap = nullptr;
+        return PKR_ECUDA;
+    }
+    if (P->gexec) {
+        cudaGraphExecDestroy(P->gexec);
+        P->gexec = nullptr;
+    }
+    const int cur = P->cur;
+    const int64_t launches = P->launches;
+    double* const Phi = P->Phi;
+    const cudaStream_t stream = P->stream;
+    P->stream = P->cap;
+    P->stop_arg = &P->ctl->stop;
+    P->gtol = tol;
+    P->gkind = tol_kind;
+    cudaGraph_t g = nullptr;
+    int rc = cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess
+                 ? PKR_OK
+                 : PKR_ECUDA;
+    if (rc == PKR_OK) {
+        for (int j = 0; j < kGraphSteps && rc == PKR_OK; ++j) {
+            P->gj = j;
+            rc = launch_one(P, kCheck, false);
+        }
+        if (cudaStreamEndCapture(P->cap, &g) != cudaSuccess) rc = PKR_ECUDA;
+    }
+    if (rc == PKR_OK && cudaGraphInstantiate(&P->gexec, g, 0) != cudaSuccess) {
+        P->gexec = nullptr;
+        rc = PKR_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    P->stream = stream;
+    P->stop_arg = nullptr;
+    P->cur = cur;
+    P->launches = launches;
+    P->Phi = Phi;
+    if (rc != PKR_OK) {
+        cudaGetLastError();
+        return rc;
+    }
+    P->gcur = cur;
     return PKR_OK;
 }
 
@@ -453,14 +543,15 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
     P->nsm = nsm;
     P->ntiles = tiles_of(p->n);
     const int nvar = variant_count(p->lattice);
-    int var = (p->variant >= 0) ? p->variant : default_variant(p->lattice, p->precision);
+    int var = (p->variant >= 0) ? p->variant : default_variant(p->lattice, p->precision, P->V, nsm);
     if (p->precision == PKR_FP16) var = 0;   // one geometry for binary16 storage
     if (var >= nvar) {
         delete P;
         return PKR_EINVAL;
     }
     if (P->stencil) {
-        int64_t g = (P->V + 255) / 256;
+        const int tb = stencil_block(P->V, nsm);
+        int64_t g = (P->V + tb - 1) / tb;
         if (g > (int64_t)nsm * 8) g = (int64_t)nsm * 8;
         P->grid = (int)g;
         P->variant = 0;
@@ -531,6 +622,10 @@ int pkr_plan_destroy(pkr_plan* P)
     cudaFree(P->fxF);
     cudaFree(P->fxmax);
     if (P->host) cudaFreeHost(P->host);
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    cudaFree(P->ctl);
+    if (P->hctl) cudaFreeHost(P->hctl);
+    if (P->cap) cudaStreamDestroy(P->cap);
     delete P;
     return PKR_OK;
 }
@@ -739,7 +834,42 @@ int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check
     double min_res = INFINITY;
     int nchecks = 0;
     int64_t done = 0;
-    for (int64_t j = 0; j < steps; ++j) {
+    bool stopped = false;
+    // Binary64 runs that check every step (the per-step stopping rules of
+    // small problems): steps go in captured graphs of kGraphSteps, the rule is
+    // applied on the device after each check, and the host reads the outcome
+    // once per graph instead of once per step.  Same steps, same stopping step.
+    if (K == 1 && tol > 0.0 && P->prob.precision == PKR_FP64 && steps >= kGraphSteps) {
+        bool ok = true;
+        if (!P->gexec || P->gcur != P->cur || P->gtol != tol || P->gkind != tol_kind)
+            ok = capture_steps(P, tol, tol_kind) == PKR_OK;
+        if (ok) {
+            *P->hctl = RunCtl{0, PKR_OK, -1, 0, INFINITY, P->last_residual};
+            PKR_CK(cudaMemcpyAsync(P->ctl, P->hctl, sizeof(RunCtl), cudaMemcpyHostToDevice,
+                                   P->stream));
+            while (steps - done >= kGraphSteps) {
+                PKR_CK(cudaGraphLaunch(P->gexec, P->stream));
+                PKR_CK(cudaMemcpyAsync(P->hctl, P->ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost,
+                                       P->stream));
+                PKR_CK(cudaStreamSynchronize(P->stream));
+                const RunCtl c = *P->hctl;
+                const int64_t ran = c.stop ? (int64_t)c.done_at + 1 : (int64_t)kGraphSteps;
+                P->launches += ran;
+                done += ran;
+                if (ran & 1) P->cur ^= 1;
+                if (P->stencil) P->Phi = P->Ps[P->cur];
+                P->last_residual = c.last_res;
+                nchecks = c.nchecks;
+                min_res = c.min_res;
+                if (c.stop) {
+                    status = c.status;
+                    stopped = true;
+                    break;
+                }
+            }
+        }
+    }
+    for (int64_t j = stopped ? steps : done; j < steps; ++j) {
         const int64_t k = P->launches;  // this launch computes Phi^k
         int mode = kPlain;
         if (k % K == 0) mode = kCheck;

@@ -95,6 +95,21 @@ struct SweepArgs {
     int* fxF;
     unsigned long long* fxmax;
     long long cfx;
+    // device flag: when it is set the launch returns at once (steps queued in
+    // a captured graph after the solve has stopped); nullptr: never
+    const int* stop;
+};
+
+// State of a device-side stopping rule (a captured run of check steps):
+// after each check the rule of pkr_plan_run is applied on the device and the
+// remaining steps of the graph see stop != 0 and do nothing.
+struct RunCtl {
+    int stop;         // 1 once converged or diverged
+    int status;       // PKR_OK or PKR_EDIVERGED
+    int done_at;      // index (in the graph) of the step that stopped
+    int nchecks;      // checks so far in this run
+    double min_res;   // smallest residual so far in this run
+    double last_res;  // last checked residual
 };
 
 
@@ -105,7 +120,16 @@ int launch_finalize_mean(const double* partials, int nblocks, int64_t V, double*
                          void* stream);
 int launch_make_source(const double* rho, const double* mean, double scale, int64_t V,
                        void* S, int precision, void* stream);
+// Threads per block of the scalar stencil: 64 on grids too small to give
+// every SM a 256-thread block, else 256.  A launch of `grid` blocks over V
+// sites used 64 exactly when grid * 64 >= V.
+inline int stencil_block(int64_t V, int nsm) { return V < (int64_t)nsm * 256 ? 64 : 256; }
+
 int launch_finalize_residual(const double* partials, int nblocks, double* out4, void* stream);
+// finalize_residual, then the stopping rule on the device for check step j
+// of a captured run (does nothing once ctl->stop is set).
+int launch_finalize_check(const double* partials, int nblocks, double* out4, RunCtl* ctl,
+                          double tol, int tol_kind, int j, void* stream);
 
 // Batch engine kernels (sweep_*.cu / pkr_kernels.cu).
 int launch_batch_step(int lattice, int precision, int variant, BatchState* state, int check_every,

@@ -83,8 +83,9 @@ __global__ void make_source_kernel(const double* __restrict__ rho, const double*
 
 // out4[0] = max |dPhi|, out4[1] = ||dPhi||_2 / ||Phi||_2 (0 if both vanish,
 // +inf if only Phi does), out4[2] = ||Phi||_2, out4[3] = sum Phi (the mass).
-__global__ void __launch_bounds__(kRedThreads)
-finalize_residual_kernel(const double* __restrict__ partials, int n, double* out4)
+// One block of kRedThreads; out4 is complete when thread 0 returns.
+__device__ __forceinline__ void finalize_block(const double* __restrict__ partials, int n,
+                                               double* out4, double* v4 = nullptr)
 {
     __shared__ double s0[kRedThreads / 32], s1[kRedThreads / 32], s2[kRedThreads / 32],
         s3[kRedThreads / 32];
@@ -123,7 +124,59 @@ finalize_residual_kernel(const double* __restrict__ partials, int n, double* out
             out4[0] = NAN;
             out4[1] = NAN;
         }
+        if (v4) {   // the same values, in registers of thread 0
+            const bool bad = !(a == a) || !(b == b);
+            v4[0] = bad ? NAN : c;
+            v4[1] = bad ? NAN : ((b > 0.0) ? sqrt(a) / sqrt(b) : (a == 0.0 ? 0.0 : INFINITY));
+            v4[2] = sqrt(b);
+            v4[3] = d;
+        }
     }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+finalize_residual_kernel(const double* __restrict__ partials, int n, double* out4)
+{
+    finalize_block(partials, n, out4);
+}
+
+// finalize_residual followed, in thread 0, by the stopping rule of
+// pkr_plan_run applied on the device (check step j of a captured run).
+// Non-finite out4[0] or out4[2], or growth by 1e6 over the smallest residual
+// after two checks, stop with PKR_EDIVERGED; a residual below tol stops with
+// PKR_OK.  Once stopped it does nothing.
+__global__ void __launch_bounds__(kRedThreads)
+finalize_check_kernel(const double* __restrict__ partials, int n, double* out4, RunCtl* ctl,
+                      double tol, int tol_kind, int j)
+{
+    if (ctl->stop) return;
+    // thread 0 reads the rule's state while the block reduces
+    int nc = 0;
+    double min_res = 0.0;
+    if (threadIdx.x == 0) {
+        nc = ctl->nchecks + 1;
+        min_res = ctl->min_res;
+    }
+    double v4[4];
+    finalize_block(partials, n, out4, v4);
+    if (threadIdx.x != 0) return;
+    const double r = v4[tol_kind == PKR_TOL_MAX_ABS_DPHI ? 0 : 1];
+    RunCtl o = *ctl;
+    o.last_res = r;
+    o.nchecks = nc;
+    if (!isfinite(v4[0]) || !isfinite(v4[2]) || (nc > 2 && r > 1e6 * min_res && r > 1e-300)) {
+        o.status = PKR_EDIVERGED;
+        o.stop = 1;
+        o.done_at = j;
+    } else {
+        if (r < min_res) o.min_res = r;
+        if (tol > 0.0 && r < tol) {
+            o.status = PKR_OK;
+            o.stop = 1;
+            o.done_at = j;
+        }
+    }
+    *ctl = o;
 }
 
 // Per-grid residual of a batch check step: sums the grid's tile partials in
@@ -369,6 +422,14 @@ int launch_make_source(const double* rho, const double* mean, double scale, int6
 int launch_finalize_residual(const double* partials, int nblocks, double* out4, void* stream)
 {
     finalize_residual_kernel<<<1, kRedThreads, 0, (cudaStream_t)stream>>>(partials, nblocks, out4);
+    return (int)cudaGetLastError();
+}
+
+int launch_finalize_check(const double* partials, int nblocks, double* out4, RunCtl* ctl,
+                          double tol, int tol_kind, int j, void* stream)
+{
+    finalize_check_kernel<<<1, kRedThreads, 0, (cudaStream_t)stream>>>(partials, nblocks, out4,
+                                                                       ctl, tol, tol_kind, j);
     return (int)cudaGetLastError();
 }
 

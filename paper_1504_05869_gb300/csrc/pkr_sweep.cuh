@@ -497,6 +497,7 @@ template <class L, typename T, int G_, int TILES_>
 __global__ void __launch_bounds__(G_ * TILES_ * 32)
 sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
 {
+    if (a.stop != nullptr && *a.stop != 0) return;   // the run stopped before this step
     constexpr int G = G_;
     constexpr int TILES = TILES_;
     using ST = Staged<L, T, G, TILES>;
@@ -891,8 +892,9 @@ template <class L>
 __global__ void __launch_bounds__(256)
 stencil_kernel(const double* __restrict__ Pin, double* __restrict__ Pout,
                const double* __restrict__ St, const Coefs<double> c, int64_t V, int nx, int ny,
-               int nz, int small, int check, double* partials)
+               int nz, int small, int check, double* partials, const int* stop)
 {
+    if (stop != nullptr && *stop != 0) return;   // the run stopped before this step
     constexpr int Q = L::Q;
     constexpr int RC = reach_of<L>();
     constexpr int W = 2 * RC + 1;
@@ -954,7 +956,7 @@ stencil_kernel(const double* __restrict__ Pin, double* __restrict__ Pout,
         __syncthreads();
         if (threadIdx.x == 0) {
             double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
                 t0 += red[k][0];
                 t1 += red[k][1];
                 t2 = fmax(t2, red[k][2]);
@@ -971,10 +973,11 @@ stencil_kernel(const double* __restrict__ Pin, double* __restrict__ Pout,
 template <class L>
 int launch_stencil(const double* Pin, double* Pout, const double* St, const Coefs<double>& c,
                    int64_t V, int nx, int ny, int nz, int small, int check, double* partials,
-                   int grid, void* stream)
+                   int grid, void* stream, const int* stop)
 {
-    stencil_kernel<L><<<grid, 256, 0, (cudaStream_t)stream>>>(Pin, Pout, St, c, V, nx, ny, nz,
-                                                              small, check, partials);
+    const int block = (int64_t)grid * 64 >= V ? 64 : 256;   // see stencil_block
+    stencil_kernel<L><<<grid, block, 0, (cudaStream_t)stream>>>(Pin, Pout, St, c, V, nx, ny, nz,
+                                                                small, check, partials, stop);
     return (int)cudaGetLastError();
 }
 
@@ -1041,7 +1044,8 @@ int variant_count_t() { return Variants<L>::N; }
     template int launch_sweep_h16<L>(const SweepArgs&, const void*, int, void*);             \
     template int occupancy_h16<L>(int*, int*);                                               \
     template int launch_stencil<L>(const double*, double*, const double*, const Coefs<double>&,  \
-                                   int64_t, int, int, int, int, int, double*, int, void*);      \
+                                   int64_t, int, int, int, int, int, double*, int, void*,       \
+                                   const int*);                                                 \
     template int launch_batch_t<L, double>(int, BatchState*, int, int, void*);               \
     template int launch_batch_t<L, float>(int, BatchState*, int, int, void*);                \
     template int batch_occupancy_t<L, double>(int, int*);                                    \

@@ -433,19 +433,56 @@ def test_converged_fx64(pk):
     assert np.array_equal(a, got)
 
 
-@pytest.mark.parametrize("tau,precision", [(1.3, "fp64"), (1.0, "fp64"), (1.3, "fp32")])
-def test_overflowing_source_reports_divergence(pk, tau, precision):
+@pytest.mark.parametrize("tau,precision,every", [(1.3, "fp64", 4), (1.0, "fp64", 4),
+                                                 (1.3, "fp32", 4), (1.3, "fp64", 1),
+                                                 (1.0, "fp64", 1)])
+def test_overflowing_source_reports_divergence(pk, tau, precision, every):
     """A permittivity so small that the source overflows to +-inf makes the
     populations and the residual non-finite: the solve stops at its next
-    check with PKR_EDIVERGED (tau_lb = 1 exercises the scalar-stencil path)
+    check with PKR_EDIVERGED (tau_lb = 1 exercises the scalar-stencil path;
+    checks every step in binary64 exercise the device-side stopping rule)
     and leaves Phi untouched."""
     import torch
     rho = _rand((8, 9, 10), 3)
     prob = pk.problem("D3Q111", rho.shape, 5, tau_lb=tau, epsilon=1e-320, tol=1e-10,
-                      check_every=4, max_sweeps=64, precision=precision)
+                      check_every=every, max_sweeps=200, precision=precision)
     r = torch.from_numpy(rho).cuda()
     phi = torch.full_like(r, 7.0)
     with pytest.raises(pk.PkrError) as e:
         pk.solve(r, phi, prob)
     assert e.value.status == -5
     assert bool((phi == 7.0).all())
+
+
+@pytest.mark.parametrize("lattice,order,shape,tau", [
+    ("D2Q169", 7, (24, 20), 6.04398),     # population sweep
+    ("D2Q169", 7, (16, 12), 1.0),         # tau_lb = 1: scalar stencil
+    ("D3Q111", 5, (10, 9, 8), 1.3),
+])
+def test_per_step_checks_in_captured_graphs(pk, lattice, order, shape, tau):
+    """Binary64 solves that check every step run their steps in captured
+    graphs that apply the stopping rule on the device.  The stopping step and
+    Phi equal the oracle's, and equal bit for bit a run stepped from the host
+    one step per call (below the graph length, so the host applies the rule)."""
+    import torch
+    rho = _rand(shape, 21)
+    tol = 1e-11
+    ref = oracle.solve(rho, lattice, order, tau_lb=tau, tol=tol, tol_kind=0, check_every=1,
+                       max_steps=100000)
+    got, rc, st = _gpu_solve(pk, rho, lattice, order, tau, tol=tol, tol_kind="max_abs",
+                             check_every=1, max_sweeps=100000)
+    assert rc == 0 and st["sweeps"] == ref.steps, (st["sweeps"], ref.steps)
+    assert st["residual"] < tol
+    assert _rel(got, ref.phi) <= FP64_TOL
+    prob = pk.problem(lattice, shape, order, tau_lb=tau, max_sweeps=100000)
+    r = torch.from_numpy(rho).cuda()
+    with pk.Plan(prob) as P:
+        P.load_source(r)
+        for _ in range(100000):
+            rc1, s1 = P.run(1, tol=tol, tol_kind="max_abs", check_every=1)
+            assert rc1 == 0
+            if s1["residual"] < tol:
+                break
+        host = P.phi(torch.empty_like(r)).cpu().numpy()
+        assert P.steps() == st["sweeps"]
+    assert np.array_equal(host, got)
