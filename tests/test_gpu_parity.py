@@ -409,7 +409,8 @@ def test_tau1_converged_and_mixed(pk):
 ])
 def test_fixed_steps_fx64(pk, lattice, order, shape, tau):
     """64-bit fixed-point storage: same 1e-12 bar as binary64 (every stored
-    value keeps >= 54 bits relative to the largest; the density sum is exact)."""
+    value is resolved to 2^-51 of the largest or finer; the density sum is
+    exact).  tau_lb = 0.75 has omega > 1: a negative relaxation coefficient."""
     rho = _rand(shape, 22)
     for steps in (1, 2, 17):
         got, rc, st = _gpu_solve(pk, rho, lattice, order, tau, steps=steps, precision="fx64")
@@ -418,17 +419,23 @@ def test_fixed_steps_fx64(pk, lattice, order, shape, tau):
         assert _rel(got, ref) <= FP64_TOL, (steps, _rel(got, ref))
 
 
-def test_converged_fx64(pk):
-    shape = (12, 10, 14)
+@pytest.mark.parametrize("lattice,order,shape,tau", [
+    ("D3Q111", 5, (12, 10, 14), 1.3),
+    ("D3Q111", 5, (12, 10, 14), 0.8),     # omega > 1
+    ("D2Q169", 7, (20, 18), 1.0),
+])
+def test_converged_fx64(pk, lattice, order, shape, tau):
+    """Converged fixed-point solves: the scale is lowered many times along the
+    way (the populations grow ~10^3x from the first step), with the same
+    stopping step and 1e-12 bar as the binary64 oracle, deterministically."""
     rho, _ = stiff_source(shape, count=6, sigma=1.5, seed=23)
-    ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.3, tol=1e-10, tol_kind=1, check_every=8,
+    ref = oracle.solve(rho, lattice, order, tau_lb=tau, tol=1e-10, tol_kind=1, check_every=8,
                        max_steps=200000)
-    got, rc, st = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-10, check_every=8,
+    got, rc, st = _gpu_solve(pk, rho, lattice, order, tau, tol=1e-10, check_every=8,
                              max_sweeps=200000, precision="fx64")
     assert rc == 0 and st["sweeps"] == ref.steps
     assert _rel(got, ref.phi) <= FP64_TOL
-    # the fixed-point scale was lowered along the way (values grew ~10^3x)
-    a, _, _ = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-10, check_every=8,
+    a, _, _ = _gpu_solve(pk, rho, lattice, order, tau, tol=1e-10, check_every=8,
                          max_sweeps=200000, precision="fx64")
     assert np.array_equal(a, got)
 
