@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 SHAPE = (256, 256, 256)
 LATTICE, ORDER, KN = "D3Q111", 5, 0.2
 PRECISION = "fp64"
+TAU = 0.0            # > 0: tau_lb directly instead of the Knudsen number
 SWEEPS_PER_STEP = 32
 SLAB = 64            # planes of the CPU-baseline sample
 REF_SLAB = 2         # planes per reference-arm step
@@ -57,16 +58,17 @@ def source():
 def configure(args):
     """Smaller or different cases (profiling, sweeps of sizes); the default is
     the headline workload."""
-    global SHAPE, LATTICE, ORDER, PRECISION, WORKLOAD
+    global SHAPE, LATTICE, ORDER, PRECISION, WORKLOAD, TAU
     if args.size:
         SHAPE = (args.size,) * 3
     LATTICE, ORDER, PRECISION = args.lattice, args.order, args.precision
     if PRECISION == "mixed":
         raise SystemExit("--precision mixed applies to the batch and serve workloads")
-    if (SHAPE, LATTICE, ORDER, PRECISION) != ((256, 256, 256), "D3Q111", 5, "fp64"):
+    TAU = args.tau
+    if (SHAPE, LATTICE, ORDER, PRECISION, TAU) != ((256, 256, 256), "D3Q111", 5, "fp64", 0.0):
         n = SHAPE[0]
         WORKLOAD = (f"poisson3d_{n}cube_{LATTICE.lower()}_n{ORDER}_{PRECISION}"
-                    f"_64gauss_sigma2_seed0_kn0.2")
+                    f"_64gauss_sigma2_seed0_" + (f"tau{TAU:g}" if TAU > 0 else "kn0.2"))
 
 
 class ClockSampler:
@@ -222,8 +224,10 @@ def run(args):
     rho = source()
     V = rho.size
     stream = torch.cuda.Stream()
-    prob = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN, tol=0.0,
+    prob = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN, tau_lb=TAU, tol=0.0,
                       check_every=SWEEPS_PER_STEP, max_sweeps=10 ** 9, precision=PRECISION)
+    # tau_lb = 1 in binary64 runs the scalar stencil (Phi-only state)
+    stencil = TAU == 1.0 and PRECISION == "fp64"
     r_dev = torch.from_numpy(rho).cuda()
     with torch.cuda.stream(stream):
         plan = pk.Plan(prob, stream=stream)
@@ -264,6 +268,8 @@ def run(args):
         dist.barrier()
     glups = total_updates / (dev_ms * 1e-3) / 1e9
     bytes_site = 2 * Q * esize + (8 if PRECISION in ("fp64", "fx64") else 4)
+    if stencil:
+        bytes_site = 24      # read Phi and the summed source, write Phi
     # per-launch: plain sweeps move 2*Q*8 + 8 bytes per site
     launch_ms = dev_ms / sweeps
     achieved = V * bytes_site / (launch_ms * 1e-3) / 1e9
@@ -281,7 +287,8 @@ def run(args):
     if not args.no_e2e:
         rho_h = torch.from_numpy(rho).pin_memory()
         phi_h = torch.empty_like(rho_h).pin_memory()
-        eprob = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN, tol=1e-10, tol_kind="rel_l2",
+        eprob = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN, tau_lb=TAU, tol=1e-10,
+                           tol_kind="rel_l2",
                            check_every=SWEEPS_PER_STEP, max_sweeps=200000,
                            precision=PRECISION)
         torch.cuda.synchronize()
@@ -304,6 +311,21 @@ def run(args):
         cpu = cpu_baseline(rho, tau)
         cpu_omp = cpu_baseline_openmp(rho, tau)
 
+    if stencil:
+        # binary64 FMA bound: Q FMAs per site; peak from the GB300's nominal
+        # FP64 rate (1.25 TFLOP/s = 625 G FMA/s)
+        fma_s = V * Q / (launch_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": fma_s, "peak": 625.0, "unit": "GFMA/s",
+                    "frac": fma_s / 625.0, "traffic": None, "peak_source": "nominal FP64",
+                    "kernel": f"stencil_kernel<{LATTICE}>", "hbm_gbs": achieved,
+                    "algorithmic_bytes_per_launch": V * bytes_site}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": achieved / hbm_peak,
+                    "traffic": recorded_traffic(), "peak_source": peak_src,
+                    "kernel": f"sweep_staged_kernel<{LATTICE},"
+                              f"{ {'fp64': 'double', 'fx64': 'long long'}.get(PRECISION, 'float') }>",
+                    "algorithmic_bytes_per_launch": V * bytes_site}
     if rank == 0:
         line = {
             "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world,
@@ -312,18 +334,13 @@ def run(args):
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fx64": "int64 (fixed point)", "fp32": "f32",
                       "fp16": "f16"}[PRECISION], "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(SHAPE), "lattice": LATTICE,
-                       "order": ORDER, "knudsen": KN, "tau_lb": tau,
+                       "order": ORDER, "knudsen": None if TAU > 0 else KN, "tau_lb": tau,
                        "sweeps_per_step": SWEEPS_PER_STEP, "residual_check": "rel_l2 fp64",
                        "kernel_variant": variant,
                        "l2": "inputs larger than L2 (2 x 14.9 GB populations)",
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs": V * bytes_site * sweeps * world / (dev_ms * 1e-3) / 1e9,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                         "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "traffic": recorded_traffic(), "peak_source": peak_src,
-                         "kernel": f"sweep_staged_kernel<{LATTICE},"
-                                   f"{ {'fp64': 'double', 'fx64': 'long long'}.get(PRECISION, 'float') }>",
-                         "algorithmic_bytes_per_launch": V * bytes_site},
+            "roofline": roofline,
             "cpu_baseline": cpu, "cpu_baseline_openmp": cpu_omp, "e2e": e2e,
             "clocks": clocks, "gpu_launches": args.steps * (SWEEPS_PER_STEP + 1),
             "wall_s": wall,
@@ -737,6 +754,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--tol", type=float, default=0.0)
+    ap.add_argument("--tau", type=float, default=0.0,
+                    help="sweep workload: tau_lb instead of Kn 0.2 (1.0 in fp64: the stencil)")
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch(args)
