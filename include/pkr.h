@@ -261,8 +261,9 @@ int pkr_solve(const pkr_problem *problem, const double *rho, double *phi, int ho
  * problem: lattice, n, order, tau_lb (or knudsen), epsilon are used; tol,
  * check_every, max_sweeps, precision and variant are ignored (binary64
  * throughout).  rho, phi: as pkr_solve (device, or host with host_buffers).
- * Device memory: V doubles + (nx/2+1) ny nz complex doubles + cuFFT's plan
- * work area, allocated and freed inside the call.  Synchronises the stream.
+ * Device memory: V doubles + (nx/2+1) ny nz complex doubles + nx+ny+nz
+ * complex phase-table entries + cuFFT's plan work area, allocated and freed
+ * inside the call.  Synchronises the stream.
  * stats: rho_mean_removed, tau_lb, cs2, wall_ms (others 0).
  * Errors (phi untouched on each): PKR_EINVAL (bad problem, V > 2^31 - 1,
  * tau_lb <= 1/2, non-finite rho), PKR_EUNSTABLE (tau_lb outside the stable

@@ -12,7 +12,8 @@
 // The denominator is small near k = 0 (it vanishes like |k|^2); since the phi_i
 // sum to one it is written as sum_i phi_i Re[(1 - e_i) / (1 - (1 - w) e_i)]
 // with 1 - cos(theta) = 2 sin^2(theta / 2), so no term cancels.  The phase
-// theta = k.v_i is reduced exactly on the integers (m v mod n) before sincospi.
+// theta = k.v_i is reduced exactly on the integers (m v mod n) and its half
+// angle built from per-axis tables of exp(-i pi j / n).
 // The transforms are cuFFT's; the transfer function T(k) is this file's kernel.
 #include <cuda_runtime.h>
 #include <cufft.h>
@@ -36,9 +37,24 @@ struct FftCoefs {
     double omega;
 };
 
-// Multiply the half spectrum S(k) (nx/2 + 1 modes along x) by T(k).
+// H[j] = exp(-i pi j / n), j < n: the half-angle phase of one axis.
+__global__ void half_phase_kernel(double2* __restrict__ H, int n)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi((double)j / n, &sn, &cs);
+        H[j] = make_double2(cs, -sn);
+    }
+}
+
+// Multiply the half spectrum S(k) (nx/2 + 1 modes along x) by T(k).  For a
+// velocity v, theta = k.v = 2 pi sum_a (m_a v_a mod n_a) / n_a; the indices
+// are reduced exactly on the integers and the half-angle phase
+// h = exp(-i theta / 2) is the product of three table entries.  Then
+// e = h^2 and 1 - cos(theta) = 2 Im(h)^2 (no cancellation near k = 0).
 __global__ void transfer_kernel(cufftDoubleComplex* __restrict__ sk, int nx, int ny, int nz,
-                                const FftCoefs c)
+                                const FftCoefs c, const double2* __restrict__ Hx,
+                                const double2* __restrict__ Hy, const double2* __restrict__ Hz)
 {
     const int nxh = nx / 2 + 1;
     const int64_t total = (int64_t)nxh * ny * nz;
@@ -55,23 +71,21 @@ __global__ void transfer_kernel(cufftDoubleComplex* __restrict__ sk, int nx, int
         }
         double num = 0.0, den = 0.0;
         for (int p = 0; p < c.npairs; ++p) {
-            // theta / (2 pi) = (mx vx / nx + my vy / ny + mz vz / nz) mod 1, in [0, 3)
-            const int64_t ax = (((int64_t)mx * c.vx[p]) % nx + nx) % nx;
-            const int64_t ay = (((int64_t)my * c.vy[p]) % ny + ny) % ny;
-            const int64_t az = (((int64_t)mz * c.vz[p]) % nz + nz) % nz;
-            const double r = (double)ax / nx + (double)ay / ny + (double)az / nz;
-            double sn, cs;
-            sincospi(2.0 * r, &sn, &cs);       // e = cs - i sn
-            const double sh = sinpi(r);
-            const double omc = 2.0 * sh * sh;  // 1 - cos(theta)
-            // d = 1 - (1 - w) e
+            const int jx = (int)((((int64_t)mx * c.vx[p]) % nx + nx) % nx);
+            const int jy = (int)((((int64_t)my * c.vy[p]) % ny + ny) % ny);
+            const int jz = (int)((((int64_t)mz * c.vz[p]) % nz + nz) % nz);
+            const double2 a = __ldg(Hx + jx), b = __ldg(Hy + jy), d = __ldg(Hz + jz);
+            const double tr = a.x * b.x - a.y * b.y, ti = a.x * b.y + a.y * b.x;
+            const double hr = tr * d.x - ti * d.y, hi = tr * d.y + ti * d.x;   // h
+            const double cs = hr * hr - hi * hi;      // e = h^2 = cs - i sn
+            const double sn = -2.0 * hr * hi;
+            const double omc = 2.0 * hi * hi;         // 1 - cos(theta)
+            // d = 1 - (1 - w) e;  Re q = Re[e conj(d)] / |d|^2;
+            // Re[(1 - e) / d] = Re[(1 - e) conj(d)] / |d|^2
             const double dr = 1.0 - cw * cs, di = cw * sn;
-            const double dd = dr * dr + di * di;
-            // Re q = Re[e conj(d)] / |d|^2 ; Re[(1 - e) / d] = Re[(1 - e) conj(d)] / |d|^2
-            const double qr = (cs * dr - sn * di) / dd;
-            const double ur = (omc * dr + sn * di) / dd;
-            num += c.mult[p] * c.chi[p] * qr;
-            den += c.mult[p] * c.phi[p] * ur;
+            const double inv = 1.0 / (dr * dr + di * di);
+            num += c.mult[p] * c.chi[p] * ((cs * dr - sn * di) * inv);
+            den += c.mult[p] * c.phi[p] * ((omc * dr + sn * di) * inv);
         }
         const double T = num / den;
         sk[m].x *= T;
@@ -142,12 +156,15 @@ extern "C" int pkr_fixed_point_fft(const pkr_problem* p, const double* rho, doub
     double* d_mean = nullptr;
     double* d_part = nullptr;
     int* d_flag = nullptr;
+    double2* d_h = nullptr;             // half-angle phase tables of x, y, z
     const int red_blocks = 152 * 4;
     if (cudaMalloc((void**)&d_r, (size_t)V * 8) != cudaSuccess ||
         cudaMalloc((void**)&d_k, nspec * sizeof(cufftDoubleComplex)) != cudaSuccess ||
         cudaMalloc((void**)&d_mean, 8) != cudaSuccess ||
         cudaMalloc((void**)&d_part, red_blocks * 8) != cudaSuccess ||
-        cudaMalloc((void**)&d_flag, sizeof(int)) != cudaSuccess) {
+        cudaMalloc((void**)&d_flag, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&d_h, (size_t)(nx + ny + nz) * sizeof(double2)) != cudaSuccess) {
+        cudaFree(d_h);
         cudaFree(d_r);
         cudaFree(d_k);
         cudaFree(d_mean);
@@ -191,7 +208,11 @@ extern "C" int pkr_fixed_point_fft(const pkr_problem* p, const double* rho, doub
         if (ok) {
             int blocks = (int)((nspec + 255) / 256);
             if (blocks > 152 * 16) blocks = 152 * 16;
-            transfer_kernel<<<blocks, 256, 0, s>>>(d_k, nx, ny, nz, c);
+            half_phase_kernel<<<(nx + 255) / 256, 256, 0, s>>>(d_h, nx);
+            half_phase_kernel<<<(ny + 255) / 256, 256, 0, s>>>(d_h + nx, ny);
+            half_phase_kernel<<<(nz + 255) / 256, 256, 0, s>>>(d_h + nx + ny, nz);
+            transfer_kernel<<<blocks, 256, 0, s>>>(d_k, nx, ny, nz, c, d_h, d_h + nx,
+                                                  d_h + nx + ny);
             ok = cudaGetLastError() == cudaSuccess;
         }
         ok = ok && cufftExecZ2D(inv, d_k, d_r) == CUFFT_SUCCESS;
@@ -213,6 +234,7 @@ extern "C" int pkr_fixed_point_fft(const pkr_problem* p, const double* rho, doub
     cudaFree(d_mean);
     cudaFree(d_part);
     cudaFree(d_flag);
+    cudaFree(d_h);
     if (flag) return PKR_EINVAL;
     if (!ok) return PKR_ECUDA;
     if (st) {
