@@ -290,13 +290,16 @@ int pkr_fixed_point_fft(const pkr_problem *problem, const double *rho, double *p
  * tolerance finish in binary32.  Its budget reservation per request is the
  * binary32 state + the binary64 state + Phi (both states exist while it is
  * converted); the binary32 share is released at the switch.
+ * A PKR_FX64 context stores every grid in 64-bit fixed point, each grid with
+ * its own pair of array exponents, rescaled on the device after every step.
  * --------------------------------------------------------------------- */
 typedef struct pkr_ctx pkr_ctx;
 
 typedef struct pkr_ctx_config {
     int32_t lattice;          /* pkr_lattice of every request */
     int32_t order;            /* expansion order N of every request */
-    int32_t precision;        /* PKR_FP64, PKR_FP32 or PKR_MIXED, for every request */
+    int32_t precision;        /* PKR_FP64, PKR_FP32, PKR_FX64 or PKR_MIXED, for every
+                                 request */
     int32_t check_every;      /* K: steps per graph replay and per residual check (>= 1) */
     size_t hbm_budget_bytes;  /* device bytes the live requests may hold */
     int32_t variant;          /* >= 0: kernel geometry; -1: library default;

@@ -40,14 +40,16 @@ namespace {
 template <class L>
 int batch_launch_l(int prec, int var, BatchState* st, int K, int grid, void* s)
 {
-    return prec == PKR_FP64 ? launch_batch_t<L, double>(var, st, K, grid, s)
-                            : launch_batch_t<L, float>(var, st, K, grid, s);
+    if (prec == PKR_FP64) return launch_batch_t<L, double>(var, st, K, grid, s);
+    if (prec == PKR_FX64) return launch_batch_t<L, long long>(var, st, K, grid, s);
+    return launch_batch_t<L, float>(var, st, K, grid, s);
 }
 template <class L>
 int batch_occ_l(int prec, int var, int* b)
 {
-    return prec == PKR_FP64 ? batch_occupancy_t<L, double>(var, b)
-                            : batch_occupancy_t<L, float>(var, b);
+    if (prec == PKR_FP64) return batch_occupancy_t<L, double>(var, b);
+    if (prec == PKR_FX64) return batch_occupancy_t<L, long long>(var, b);
+    return batch_occupancy_t<L, float>(var, b);
 }
 
 }  // namespace
@@ -106,6 +108,7 @@ struct Job {
     void* pop[2] = {nullptr, nullptr};   // populations in the precision of the job's lane
     void* S = nullptr;                   // source, same precision
     double* Phi = nullptr;               // density (binary64)
+    void* fx = nullptr;                  // fixed-point lanes: int F[2], then the OR bound (u64)
     size_t bytes = 0;                    // bytes counted against the budget (reservation)
     int64_t V = 0;
     int ntiles = 0;
@@ -181,6 +184,11 @@ void fill_grid(unsigned char* dst, const Job* j, const LatticeInfo& li, int tile
     g.small = j->small;
     g.tile_begin = tile_begin;
     g.join = j->join;
+    if (j->fx) {
+        g.fxF = static_cast<int*>(j->fx);
+        g.fxmax = reinterpret_cast<unsigned long long*>(static_cast<char*>(j->fx) + 8);
+        g.cfx = std::llround(std::ldexp(1.0 - j->omega, 62));
+    }
     g.c.om1 = (R)(1.0 - j->omega);
     for (int c = 0; c < li.ncls; ++c) {
         g.c.wphi[c] = (R)(j->omega * li.cls_phi[c]);
@@ -218,7 +226,9 @@ void free_job_memory(pkr_ctx* C, Job* j)
 {
     free_lane_state(C, j);
     if (j->Phi) cudaFreeAsync(j->Phi, C->stream);
+    if (j->fx) cudaFreeAsync(j->fx, C->stream);
     j->Phi = nullptr;
+    j->fx = nullptr;
     C->used -= j->bytes;
     j->bytes = 0;
 }
@@ -253,7 +263,9 @@ int make_job_source(pkr_ctx* C, Job* j, const double* rd, int ln)
     if (cudaMemsetAsync(C->d_flag, 0, sizeof(int), C->stream) != cudaSuccess ||
         launch_rho_partials(rd, j->V, C->d_scratch, kScratchBlocks, C->d_flag, C->stream) != 0 ||
         launch_finalize_mean(C->d_scratch, kScratchBlocks, j->V, C->d_mean, C->stream) != 0 ||
-        launch_make_source(rd, C->d_mean, scale, j->V, j->S, C->lane[ln].prec, C->stream) != 0 ||
+        launch_make_source(rd, C->d_mean, scale, j->V, j->S,
+                           C->lane[ln].prec == PKR_FX64 ? PKR_FP64 : C->lane[ln].prec,
+                           C->stream) != 0 ||
         cudaMemcpyAsync(C->h_flag, C->d_flag, sizeof(int), cudaMemcpyDeviceToHost, C->stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(C->h_mean, C->d_mean, sizeof(double), cudaMemcpyDeviceToHost,
@@ -285,6 +297,34 @@ int admit(pkr_ctx* C, Job* j)
     int rc = make_job_source(C, j, rd, 0);
     if (rc != PKR_OK) return rc;
     if (cudaMemsetAsync(j->Phi, 0, (size_t)j->V * 8, C->stream) != cudaSuccess) return PKR_ECUDA;
+    if (C->lane[0].prec == PKR_FX64) {
+        // exponent of the first write (the step from zero stores chi_i S): its
+        // largest value lands near 2^52, as for a plan
+        if (cudaMallocAsync(&j->fx, 16, C->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return PKR_ENOMEM;
+        }
+        unsigned long long* mb = reinterpret_cast<unsigned long long*>(static_cast<char*>(j->fx) + 8);
+        unsigned long long hm = 0;
+        if (cudaMemsetAsync(mb, 0, 8, C->stream) != cudaSuccess ||
+            launch_absmax_f64(static_cast<const double*>(j->S), j->V, mb, C->stream) != 0 ||
+            cudaMemcpyAsync(&hm, mb, 8, cudaMemcpyDeviceToHost, C->stream) != cudaSuccess ||
+            cudaStreamSynchronize(C->stream) != cudaSuccess)
+            return PKR_ECUDA;
+        double ms = 0.0;
+        std::memcpy(&ms, &hm, sizeof(ms));
+        double mchi = 0.0;
+        for (int i = 0; i < C->li.Q; ++i) mchi = std::fmax(mchi, std::fabs(C->li.chi[i]));
+        const double m = ms * mchi;
+        int F = 0;
+        if (m > 0.0 && std::isfinite(m)) F = 52 - (std::ilogb(m) + 1);
+        const int F2[2] = {F, F};
+        if (cudaMemcpyAsync(j->fx, F2, sizeof(F2), cudaMemcpyHostToDevice, C->stream) !=
+                cudaSuccess ||
+            cudaMemsetAsync(mb, 0, 8, C->stream) != cudaSuccess ||
+            cudaStreamSynchronize(C->stream) != cudaSuccess)
+            return PKR_ECUDA;
+    }
     j->mean = *C->h_mean;
     j->lane = 0;
     j->join = C->lane[0].step;
@@ -381,8 +421,8 @@ int rebuild(pkr_ctx* C, Lane& L)
     int tb = 0;
     for (size_t k = 0; k < L.live.size(); ++k) {
         unsigned char* dst = L.h_grids.data() + k * (size_t)L.grid_stride;
-        if (L.prec == PKR_FP64) fill_grid<double>(dst, L.live[k], C->li, tb);
-        else fill_grid<float>(dst, L.live[k], C->li, tb);
+        if (L.prec == PKR_FP32) fill_grid<float>(dst, L.live[k], C->li, tb);
+        else fill_grid<double>(dst, L.live[k], C->li, tb);
         tb += L.live[k]->ntiles;
     }
     L.h_state.grids = L.d_grids;
@@ -409,6 +449,8 @@ int enqueue_window(pkr_ctx* C, Lane& L)
     for (int k = 0; k < C->K; ++k) {
         if (launch_batch_step(C->cfg.lattice, L.prec, L.variant, L.d_state, C->K, L.grid,
                               C->stream) != 0 ||
+            (L.prec == PKR_FX64 &&
+             launch_batch_fx_rescale(L.d_state, C->max_grids, C->stream) != 0) ||
             launch_batch_increment(L.d_state, C->stream) != 0)
             return PKR_ECUDA;
     }
@@ -606,9 +648,9 @@ int tune_variant(pkr_ctx* C, Lane& L, int edge);
 bool init_lane(pkr_ctx* C, Lane& L, int prec)
 {
     L.prec = prec;
-    L.elem = prec == PKR_FP64 ? 8 : 4;
-    L.grid_stride = prec == PKR_FP64 ? (int)sizeof(BatchGrid<double>)
-                                     : (int)sizeof(BatchGrid<float>);
+    L.elem = prec == PKR_FP32 ? 4 : 8;
+    L.grid_stride = prec == PKR_FP32 ? (int)sizeof(BatchGrid<float>)
+                                     : (int)sizeof(BatchGrid<double>);
     L.h_grids.assign((size_t)C->max_grids * L.grid_stride, 0);
     std::memset(&L.h_state, 0, sizeof(BatchState));
     return cudaMalloc((void**)&L.d_state, sizeof(BatchState)) == cudaSuccess &&
@@ -642,7 +684,7 @@ int pkr_ctx_create(const pkr_ctx_config* cfg, void* stream, pkr_ctx** out)
     *out = nullptr;
     if (cfg->check_every < 1 || cfg->hbm_budget_bytes == 0) return PKR_EINVAL;
     if (cfg->precision != PKR_FP64 && cfg->precision != PKR_FP32 &&
-        cfg->precision != PKR_MIXED)
+        cfg->precision != PKR_MIXED && cfg->precision != PKR_FX64)
         return PKR_EINVAL;
     LatticeInfo li;
     int rc = build_lattice(cfg->lattice, cfg->order, &li);
@@ -825,6 +867,7 @@ int pkr_ctx_destroy(pkr_ctx* C)
             if (j->pop[k]) cudaFree(j->pop[k]);
         if (j->S) cudaFree(j->S);
         if (j->Phi) cudaFree(j->Phi);
+        if (j->fx) cudaFree(j->fx);
         delete j;
     }
     for (int ln = 0; ln < 2; ++ln) free_lane(C->lane[ln]);
@@ -871,6 +914,16 @@ int tune_variant(pkr_ctx* C, Lane& L, int edge)
     cudaMemset(probe.pop[0], 0, popb);
     cudaMemset(probe.pop[1], 0, popb);
     cudaMemset(probe.S, 0, (size_t)probe.V * L.elem);
+    if (L.prec == PKR_FX64) {   // zero exponents and bound for the probe's fixed-point steps
+        if (cudaMalloc(&probe.fx, 16) != cudaSuccess) {
+            cudaGetLastError();
+            for (int k = 0; k < 2; ++k) cudaFree(probe.pop[k]);
+            cudaFree(probe.S);
+            cudaFree(probe.Phi);
+            return -1;
+        }
+        cudaMemset(probe.fx, 0, 16);
+    }
     probe.join = -1;   // never the zero-in step: the timed steps pull real data
     L.live.push_back(&probe);
     int best = -1;
@@ -908,8 +961,10 @@ int tune_variant(pkr_ctx* C, Lane& L, int edge)
     for (int k = 0; k < 2; ++k) cudaFree(probe.pop[k]);
     cudaFree(probe.S);
     cudaFree(probe.Phi);
+    cudaFree(probe.fx);
     probe.pop[0] = probe.pop[1] = probe.S = nullptr;
     probe.Phi = nullptr;
+    probe.fx = nullptr;
     return best;
 }
 

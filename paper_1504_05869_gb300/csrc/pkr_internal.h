@@ -54,6 +54,12 @@ struct BatchGrid {
     int tile_begin;        // first batch-wide tile of this grid
     int pad;
     long long join;        // batch step at which the grid starts from zero
+    // 64-bit fixed-point storage only (device memory of the grid): exponents
+    // of the two arrays, OR of |stored| over the current step, and
+    // round((1 - omega) 2^62)
+    int* fxF;
+    unsigned long long* fxmax;
+    long long cfx;
     Coefs<R> c;
 };
 
@@ -137,6 +143,9 @@ int launch_batch_step(int lattice, int precision, int variant, BatchState* state
 int batch_occupancy(int lattice, int precision, int variant, int* blocks_per_sm);
 int launch_batch_reduce(BatchState* state, int max_grids, int grid_stride_bytes, void* stream);
 int launch_batch_increment(BatchState* state, void* stream);
+// 64-bit fixed-point batches: after a step, each grid's rescale (as
+// launch_fx_rescale does for a plan), for the array its next step writes.
+int launch_batch_fx_rescale(BatchState* state, int max_grids, void* stream);
 int launch_convert(const void* in, int in_precision, void* out, int out_precision, int64_t n,
                    void* stream);
 // out[i*V + x] = in[i*V + x] - shift[i] (storage conversion with a per-plane

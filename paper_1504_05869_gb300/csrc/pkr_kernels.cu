@@ -310,6 +310,29 @@ int launch_batch_reduce(BatchState* state, int max_grids, int grid_stride_bytes,
     return (int)cudaGetLastError();
 }
 
+// One thread per grid of a 64-bit fixed-point batch, after the step and
+// before the step counter moves: the array the grid read this step (parity
+// of its age) is the one its next step writes; set its exponent from the
+// bit length of this step's largest |stored| and reset the bound.
+__global__ void batch_fx_rescale_kernel(const BatchState* st)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= st->ngrids) return;
+    const BatchGrid<double>& gd = static_cast<const BatchGrid<double>*>(st->grids)[g];
+    const int cur = (int)((st->step - gd.join) & 1);
+    const unsigned long long m = *gd.fxmax;
+    int sh = 0;
+    if (m > (1ull << 54)) sh = (64 - __clzll((long long)m)) - 52;
+    gd.fxF[cur] = gd.fxF[cur ^ 1] - sh;
+    *gd.fxmax = 0ull;
+}
+
+int launch_batch_fx_rescale(BatchState* state, int max_grids, void* stream)
+{
+    batch_fx_rescale_kernel<<<(max_grids + 127) / 128, 128, 0, (cudaStream_t)stream>>>(state);
+    return (int)cudaGetLastError();
+}
+
 int launch_batch_increment(BatchState* state, void* stream)
 {
     batch_step_increment_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(state);

@@ -614,13 +614,20 @@ sweep_batch_kernel(BatchState* st, int K)
         int mode = kPlain;
         if (age >= 1 && (age + 1) % K == 0) mode = kCheck;
         else if (zero_in || (age + 2) % K == 0) mode = kWritePhi;
+        constexpr bool fx = std::is_same<T, long long>::value;
         const TileGrid<T> tg{static_cast<const T*>(gd.pop[cur]), static_cast<T*>(gd.pop[cur ^ 1]),
                              static_cast<const typename SrcType<T>::type*>(gd.S), gd.Phi, gd.V,
-                             gd.nx, gd.ny, gd.nz, gd.small, 0.0, 0, 0, 0};
+                             gd.nx, gd.ny, gd.nz, gd.small, 0.0, fx ? gd.fxF[cur] : 0,
+                             fx ? gd.fxF[cur ^ 1] : 0, fx ? gd.cfx : 0};
         double d2 = 0.0, n2 = 0.0, mx = 0.0, ms = 0.0;
         unsigned long long fxm = 0ull;
         tile_step<L, T, G, TILES>(tg, gd.c, tile - gd.tile_begin, mode, zero_in, lane, grp, sub,
                                   sbase, xacc, xexp, d2, n2, mx, ms, fxm);
+        if constexpr (fx) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) fxm |= __shfl_down_sync(0xffffffffu, fxm, o);
+            if (lane == 0 && fxm) atomicOr(gd.fxmax, fxm);
+        }
         if (mode == kCheck && grp == 0) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -1048,7 +1055,9 @@ int variant_count_t() { return Variants<L>::N; }
                                    const int*);                                                 \
     template int launch_batch_t<L, double>(int, BatchState*, int, int, void*);               \
     template int launch_batch_t<L, float>(int, BatchState*, int, int, void*);                \
+    template int launch_batch_t<L, long long>(int, BatchState*, int, int, void*);            \
     template int batch_occupancy_t<L, double>(int, int*);                                    \
+    template int batch_occupancy_t<L, long long>(int, int*);                                 \
     template int batch_occupancy_t<L, float>(int, int*);
 
 }  // namespace pkr

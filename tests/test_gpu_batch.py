@@ -1,7 +1,8 @@
 """GPU tests of the batch / serving engine (pkr_ctx_*), through the C ABI.
 
 * Every request's Phi equals the oracle's after the number of steps the
-  engine reports (binary64: <= 1e-12 relative L2; binary32 storage: <= 2e-5,
+  engine reports (binary64 and 64-bit fixed point, each grid with its own
+  exponents: <= 1e-12 relative L2; binary32 storage: <= 2e-5,
   the binary32 rounding of each population accumulated over the run and
   bounded by the contraction).
 * A request gives the same result alone and in a mix of other requests (bit
@@ -73,7 +74,7 @@ def _run_ctx(pk, jobs, precision, K=8, budget=2 * 10 ** 9, threaded=False, host=
     return res, info
 
 
-@pytest.mark.parametrize("precision,bar", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-12), ("fp32", 2e-5), ("fx64", 1e-12)])
 def test_batch_matches_oracle(pk, precision, bar):
     res, info = _run_ctx(pk, JOBS, precision)
     assert info["finished"] == len(JOBS) and info["bytes_in_use"] == 0
@@ -86,7 +87,7 @@ def test_batch_matches_oracle(pk, precision, bar):
         assert abs(st["rho_mean_removed"] - rho.mean()) < 1e-15
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fx64"])
 def test_same_result_alone_and_in_mix(pk, precision):
     alone, _ = _run_ctx(pk, JOBS[:1], precision)
     mixed, _ = _run_ctx(pk, JOBS[1:3] + JOBS[:1] + JOBS[3:], precision)
