@@ -173,3 +173,25 @@ def test_context_config_validation(pk_cfg=None):
     assert create(variant=99) == -1
     assert create(order=7) == -1
     assert create(lattice=42) == -1
+
+
+def test_site_count_limits_rejected_on_the_host(pkr):
+    """The flat site index is 32-bit: V = 2^31 is refused (PKR_EINVAL) by
+    every entry point before any device work; 2^31 - 1 passes validation
+    (pkr_plan_bytes reports its size)."""
+    big = (1024, 1024, 2048)                       # numpy order: V = 2^31
+    assert _create(pkr, shape=big)[0] == -1
+    p = pkr.problem("D3Q111", big, 5, tau_lb=1.0)
+    b = ctypes.c_size_t()
+    assert pkr._pkr.pkr_plan_bytes(ctypes.byref(p), ctypes.byref(b)) == -1
+    st = pkr._pkr.pkr_stats()
+    dummy = ctypes.c_void_p(16)                    # never dereferenced: refused first
+    assert pkr._pkr.pkr_solve(ctypes.byref(p), dummy, dummy, 0, ctypes.byref(st), None) == -1
+    assert pkr._pkr.pkr_fixed_point_fft(ctypes.byref(p), dummy, dummy, 0, ctypes.byref(st),
+                                        None) == -1
+    ok = pkr.problem("D1Q5", (2 ** 31 - 1,), 3, tau_lb=1.0)
+    assert pkr._pkr.pkr_plan_bytes(ctypes.byref(ok), ctypes.byref(b)) == 0
+    assert b.value > 2 * 5 * (2 ** 31 - 1) * 8
+    out = (ctypes.c_double * 3)()
+    for V in (0, -5, 2 ** 31):
+        assert pkr._pkr.pkr_residual_noalloc(dummy, dummy, V, out, None) == -1
