@@ -772,8 +772,8 @@ sweep_h16_kernel(const SweepArgs a, const Coefs<float> c)
         });
         cp_async_wait_all();
 
-        // pick each lane's half and rewrite the slot as the scaled binary32
-        // value, so the passes below are those of binary32 storage
+        // pick each lane's half and rewrite the slot as a binary32 value, so
+        // the passes below are those of binary32 storage
 #pragma unroll
         for (int w = 0; w < NPB; ++w) {
             const unsigned int bits = pb[w];
@@ -783,11 +783,14 @@ sweep_h16_kernel(const SweepArgs a, const Coefs<float> c)
                 const uint32_t ad = sbase + (uint32_t)((32 * w + b) * 128);
                 const unsigned int wd = lds_b32(ad);
                 const unsigned int h = ((bits >> b) & 1u) ? (wd >> 16) : (wd & 0xffffu);
-                const float v = __half2float(__ushort_as_half((unsigned short)h)) * sr;
+                const float v = __half2float(__ushort_as_half((unsigned short)h));
                 asm volatile("st.shared.f32 [%0], %1;" ::"r"(ad), "f"(v) : "memory");
             }
         }
-        const float Phi = density_fixed_f32<Q>(sbase);
+        // the slots hold unscaled values: the array's scale sr (a power of
+        // two, so exactly) multiplies the sum and the relaxation factor
+        const float Phi = density_fixed_f32<Q>(sbase) * sr;
+        const float om1s = c.om1 * sr;
         const float Sx = valid ? (float)((double)S[s] + a.soff) : 0.f;
         if (valid) {
             static_for<0, NC>([&](auto CI) {
@@ -797,14 +800,9 @@ sweep_h16_kernel(const SweepArgs a, const Coefs<float> c)
                 unsigned short* dst = reinterpret_cast<unsigned short*>(B) + ((int64_t)i0 * V + s);
 #pragma unroll 4
                 for (int i = i0; i < i1; ++i) {
-                    const float p = fmaf(c.om1, lds_f32(sbase + (uint32_t)(i * 128)), e);
+                    const float p = fmaf(om1s, lds_f32(sbase + (uint32_t)(i * 128)), e);
                     pmax = fmaxf(pmax, fabsf(p));
-                    float q = p * inv_sw;
-                    if (fabsf(q) > 65504.f) {
-                        of = 1;
-                        q = copysignf(65504.f, q);
-                    }
-                    __stcs(dst, __half_as_ushort(__float2half_rn(q)));
+                    __stcs(dst, __half_as_ushort(__float2half_rn(p * inv_sw)));
                     dst += V;
                 }
             });
@@ -841,6 +839,8 @@ sweep_h16_kernel(const SweepArgs a, const Coefs<float> c)
             rpart[sub][3] = rms;
         }
     }
+    // a stored value beyond the binary16 range (it became +-inf) overflowed
+    of = !(pmax * inv_sw <= 65504.f);
     if (__any_sync(0xffffffffu, of) && lane == 0) atomicOr(a.oflow, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
