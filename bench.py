@@ -689,6 +689,67 @@ def run_knudsen(args):
     return 0
 
 
+def run_paper1d(args):
+    """The paper's 1D experiments on the GPU (Sec. "Computational
+    performance", Table 2): rho = sin(2 pi x / L), tau_lb = 1, converged to a
+    rel. residual of 1e-14 (checked every step, on the device); per-node error
+    against the analytic solution next to the printed Table 2 values, the
+    orders of convergence, and the L = 100 step counts next to the paper's."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+
+    def rows(name):
+        out = []
+        for line in open(os.path.join(ROOT, "tests", "golden", name)):
+            line = line.strip()
+            if line and not line.startswith("#"):
+                out.append(line.split())
+        return out
+
+    lat_for = {1: "D1Q5", 3: "D1Q5", 5: "D1Q9", 7: "D1Q13"}
+
+    def solve(N, L, tol):
+        x = np.arange(L)
+        k = 2 * np.pi / L
+        rho = np.sin(k * x)
+        prob = pk.problem(lat_for[N], (L,), N, tau_lb=1.0, tol=tol, tol_kind="rel_l2",
+                          check_every=1, max_sweeps=10 ** 6)
+        r = torch.from_numpy(rho).cuda()
+        phi = torch.empty_like(r)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = pk.solve(r, phi, prob)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        exact = rho / k ** 2
+        err = float(np.abs(phi.cpu().numpy() - exact).max() / np.abs(exact).max())
+        return err, st["sweeps"], dt, rc
+
+    table = []
+    for L, N, printed in rows("table2_per_node_error.txt"):
+        err, sw, dt, rc = solve(int(N), int(L), 1e-14)
+        table.append({"L": int(L), "N": int(N), "error": err, "paper": float(printed),
+                      "sweeps": sw, "seconds": dt, "status": rc})
+    orders = {}
+    for N in (3, 5, 7):
+        e32 = solve(N, 32, 1e-14)[0]
+        e64 = solve(N, 64, 1e-14)[0]
+        orders[N] = float(np.log2(e32 / e64))
+    steps = {}
+    paper_steps = {int(r[0]): int(r[2]) for r in rows("steps_L100.txt")}
+    for N in (1, 3, 5, 7):
+        err, sw, dt, rc = solve(N, 100, 1e-13)
+        steps[N] = {"sweeps": sw, "paper": paper_steps[N], "seconds": dt, "error": err}
+    line = {"metric": "the paper's 1D experiments on the GPU (Table 2, orders, L=100 steps)",
+            "workload": "paper1d", "value": sum(r["seconds"] for r in table), "unit": "s",
+            "higher_is_better": False, "table2": table, "orders_L32_L64": orders,
+            "steps_L100_rel_residual_1e-13": steps, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_tau1(args):
     """The paper's setting tau_lb = 1 (D3Q111 N=5): the scalar-stencil path
     against the population sweep, per step at 256^3 (64 Gaussians) and for a
@@ -755,7 +816,7 @@ def main():
                     help="sweep workload: fp64/fp32/fp16/fx64; batch/serve: fp64/fp32/mixed")
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "batch", "serve", "poisson2d", "precision", "tau1",
-                             "knudsen"])
+                             "knudsen", "paper1d"])
     ap.add_argument("--no-512", action="store_true")
     ap.add_argument("--solve-512", action="store_true",
                     help="precision workload: also solve at 512^3 against the FFT fixed point")
@@ -780,6 +841,8 @@ def main():
         return run_tau1(args)
     if args.workload == "knudsen":
         return run_knudsen(args)
+    if args.workload == "paper1d":
+        return run_paper1d(args)
     configure(args)
     if args.impl == "reference":
         return run_reference(args)
