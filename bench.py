@@ -737,6 +737,17 @@ def run_paper1d(args):
         e32 = solve(N, 32, 1e-14)[0]
         e64 = solve(N, 64, 1e-14)[0]
         orders[N] = float(np.log2(e32 / e64))
+    # Fig. 5: error and steps against L for every N, with the fits
+    # error = a_N L^-alpha_N and steps = b_N L^2 (least squares in log space)
+    fig5 = {}
+    for N in (1, 3, 5, 7):
+        Ls = [8, 16, 32, 64, 128]
+        res = [solve(N, L, 1e-14) for L in Ls]
+        lL = np.log(np.array(Ls, dtype=float))
+        alpha, loga = np.polyfit(lL, np.log([r[0] for r in res]), 1)
+        b = float(np.exp(np.mean(np.log([r[1] for r in res]) - 2 * lL)))
+        fig5[N] = {"L": Ls, "error": [r[0] for r in res], "sweeps": [r[1] for r in res],
+                   "alpha": float(-alpha), "a": float(np.exp(loga)), "b_steps_per_L2": b}
     steps = {}
     paper_steps = {int(r[0]): int(r[2]) for r in rows("steps_L100.txt")}
     for N in (1, 3, 5, 7):
@@ -745,6 +756,7 @@ def run_paper1d(args):
     line = {"metric": "the paper's 1D experiments on the GPU (Table 2, orders, L=100 steps)",
             "workload": "paper1d", "value": sum(r["seconds"] for r in table), "unit": "s",
             "higher_is_better": False, "table2": table, "orders_L32_L64": orders,
+            "fig5": fig5,
             "steps_L100_rel_residual_1e-13": steps, "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
