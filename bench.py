@@ -710,9 +710,9 @@ def run_paper1d(args):
 
     lat_for = {1: "D1Q5", 3: "D1Q5", 5: "D1Q9", 7: "D1Q13"}
 
-    def solve(N, L, tol):
+    def solve(N, L, tol, l=1):
         x = np.arange(L)
-        k = 2 * np.pi / L
+        k = 2 * np.pi * l / L
         rho = np.sin(k * x)
         prob = pk.problem(lat_for[N], (L,), N, tau_lb=1.0, tol=tol, tol_kind="rel_l2",
                           check_every=1, max_sweeps=10 ** 6)
@@ -748,6 +748,10 @@ def run_paper1d(args):
         b = float(np.exp(np.mean(np.log([r[1] for r in res]) - 2 * lL)))
         fig5[N] = {"L": Ls, "error": [r[0] for r in res], "sweeps": [r[1] for r in res],
                    "alpha": float(-alpha), "a": float(np.exp(loga)), "b_steps_per_L2": b}
+    # Figs. 1-4: the l = 1 and l = 4 sources at L = 128, 32 and 8
+    figs = {}
+    for l, L in ((1, 128), (4, 128), (4, 32), (1, 8)):
+        figs[f"l{l}_L{L}"] = {N: solve(N, L, 1e-14, l)[0] for N in (1, 3, 5, 7)}
     steps = {}
     paper_steps = {int(r[0]): int(r[2]) for r in rows("steps_L100.txt")}
     for N in (1, 3, 5, 7):
@@ -756,7 +760,7 @@ def run_paper1d(args):
     line = {"metric": "the paper's 1D experiments on the GPU (Table 2, orders, L=100 steps)",
             "workload": "paper1d", "value": sum(r["seconds"] for r in table), "unit": "s",
             "higher_is_better": False, "table2": table, "orders_L32_L64": orders,
-            "fig5": fig5,
+            "fig5": fig5, "figs_1_to_4_error": figs,
             "steps_L100_rel_residual_1e-13": steps, "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
