@@ -62,8 +62,8 @@ def configure(args):
     if args.size:
         SHAPE = (args.size,) * 3
     LATTICE, ORDER, PRECISION = args.lattice, args.order, args.precision
-    if PRECISION == "mixed":
-        raise SystemExit("--precision mixed applies to the batch and serve workloads")
+    if PRECISION in ("mixed", "mixed_fx64"):
+        raise SystemExit("--precision mixed* applies to the batch and serve workloads")
     TAU = args.tau
     if (SHAPE, LATTICE, ORDER, PRECISION, TAU) != ((256, 256, 256), "D3Q111", 5, "fp64", 0.0):
         n = SHAPE[0]
@@ -614,6 +614,7 @@ def run_precision(args):
     nref = torch.linalg.norm(ref).item()
     for label, prec, tol in (("fp64", "fp64", args.target_tol), ("mixed", "mixed", args.target_tol),
                              ("mixed16", "mixed16", args.target_tol),
+                             ("mixed_fx64", "mixed_fx64", args.target_tol),
                              ("fx64", "fx64", args.target_tol), ("fp32", "fp32", 1e-7),
                              ("fp16", "fp16", 1e-3)):
         phi, rc, st, dt = solve(prec, tol)
@@ -622,8 +623,7 @@ def run_precision(args):
                                           "launches": st["launches"], "status": rc,
                                           "tol": tol, "rel_l2_vs_fp64_fixed_point": err}
     t64 = out["time_to_1e-8_256"]["fp64"]["seconds"]
-    tmx = min(out["time_to_1e-8_256"]["mixed"]["seconds"],
-              out["time_to_1e-8_256"]["mixed16"]["seconds"])
+    tmx = min(out["time_to_1e-8_256"][m]["seconds"] for m in ("mixed", "mixed16", "mixed_fx64"))
     line = {"metric": "time to rel L2 1e-8 of the binary64 fixed point, mixed vs plain binary64",
             "workload": "precision", "value": tmx, "unit": "s", "higher_is_better": False,
             "plain_fp64_s": t64, "speedup_vs_plain_fp64": t64 / tmx, **out,
@@ -828,8 +828,9 @@ def main():
     ap.add_argument("--lattice", default="D3Q111", choices=["D3Q111", "D3Q19"])
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--precision", default="fp64",
-                    choices=["fp64", "fp32", "fp16", "fx64", "mixed"],
-                    help="sweep workload: fp64/fp32/fp16/fx64; batch/serve: fp64/fp32/mixed")
+                    choices=["fp64", "fp32", "fp16", "fx64", "mixed", "mixed_fx64"],
+                    help="sweep workload: fp64/fp32/fp16/fx64; batch/serve: "
+                         "fp64/fp32/fx64/mixed/mixed_fx64")
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "batch", "serve", "poisson2d", "precision", "tau1",
                              "knudsen", "paper1d"])

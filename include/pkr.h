@@ -86,9 +86,13 @@ typedef enum pkr_lattice {
  * so every value is resolved to 2^-51 or finer relative to the largest one:
  * about binary64's accuracy for the field as a whole (not for values many
  * orders below the largest).  On GPUs with little binary64 throughput it runs
- * the sweep on the integer units. */
+ * the sweep on the integer units.
+ * MIXED_FX64 (pkr_solve and contexts): as MIXED, with the continuation in
+ * 64-bit fixed point (FX64) instead of binary64 storage: the converted state's
+ * exponent is set from its largest magnitude.  */
 typedef enum pkr_precision {
-    PKR_FP64 = 0, PKR_FP32 = 1, PKR_MIXED = 2, PKR_FP16 = 3, PKR_MIXED16 = 4, PKR_FX64 = 5
+    PKR_FP64 = 0, PKR_FP32 = 1, PKR_MIXED = 2, PKR_FP16 = 3, PKR_MIXED16 = 4, PKR_FX64 = 5,
+    PKR_MIXED_FX64 = 6
 } pkr_precision;
 #define PKR_MIXED_SWITCH_TOL 1e-6
 #define PKR_MIXED16_SWITCH_TOL 1e-3
@@ -214,7 +218,8 @@ int pkr_plan_autotune(pkr_plan *plan, int steps_per_variant, int32_t *best_varia
  * source (the receiving plan keeps its own S).  The copied state is projected
  * onto the zero-mass gauge (mean of Phi removed through the k = 0
  * equilibrium mode), which the exact iteration from zero keeps to rounding.
- * Synchronises. */
+ * Into PKR_FX64 the exponent is set from the largest converted magnitude.
+ * Not into PKR_FP16, nor from PKR_FX64 (PKR_EINVAL).  Synchronises. */
 int pkr_plan_import(pkr_plan *plan, const pkr_plan *from);
 
 /* Queue `count` plain steps (no residual, no synchronisation).  For timing. */
@@ -292,14 +297,15 @@ int pkr_fixed_point_fft(const pkr_problem *problem, const double *rho, double *p
  * converted); the binary32 share is released at the switch.
  * A PKR_FX64 context stores every grid in 64-bit fixed point, each grid with
  * its own pair of array exponents, rescaled on the device after every step.
+ * A PKR_MIXED_FX64 context is a MIXED one whose second batch is PKR_FX64.
  * --------------------------------------------------------------------- */
 typedef struct pkr_ctx pkr_ctx;
 
 typedef struct pkr_ctx_config {
     int32_t lattice;          /* pkr_lattice of every request */
     int32_t order;            /* expansion order N of every request */
-    int32_t precision;        /* PKR_FP64, PKR_FP32, PKR_FX64 or PKR_MIXED, for every
-                                 request */
+    int32_t precision;        /* PKR_FP64, PKR_FP32, PKR_FX64, PKR_MIXED or
+                                 PKR_MIXED_FX64, for every request */
     int32_t check_every;      /* K: steps per graph replay and per residual check (>= 1) */
     size_t hbm_budget_bytes;  /* device bytes the live requests may hold */
     int32_t variant;          /* >= 0: kernel geometry; -1: library default;

@@ -11,12 +11,12 @@ import ctypes
 
 from . import _pkr
 from ._pkr import (LATTICE_DIM, LATTICES, PKR_EBUSY, PKR_FP16, PKR_FP32, PKR_FP64,  # noqa: F401
-                   PKR_FX64, PKR_MIXED, PKR_MIXED16,
+                   PKR_FX64, PKR_MIXED, PKR_MIXED16, PKR_MIXED_FX64,
                    PKR_TOL_MAX_ABS_DPHI, PKR_TOL_REL_L2_DPHI, PkrError, check, pkr_ctx_config,
                    pkr_problem, pkr_stats)
 
 PRECISIONS = {"fp64": PKR_FP64, "fp32": PKR_FP32, "mixed": PKR_MIXED, "fp16": PKR_FP16,
-              "mixed16": PKR_MIXED16, "fx64": PKR_FX64}
+              "mixed16": PKR_MIXED16, "fx64": PKR_FX64, "mixed_fx64": PKR_MIXED_FX64}
 TOL_KINDS = {"max_abs": PKR_TOL_MAX_ABS_DPHI, "rel_l2": PKR_TOL_REL_L2_DPHI}
 
 

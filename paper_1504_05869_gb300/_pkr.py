@@ -22,6 +22,7 @@ LATTICE_DIM = {"D1Q5": 1, "D1Q9": 1, "D1Q13": 1, "D2Q25": 2, "D2Q81": 2, "D2Q169
                "D3Q19": 3, "D3Q111": 3}
 # pkr_precision / pkr_tol_kind
 PKR_FP64, PKR_FP32, PKR_MIXED, PKR_FP16, PKR_MIXED16, PKR_FX64 = 0, 1, 2, 3, 4, 5
+PKR_MIXED_FX64 = 6
 PKR_TOL_MAX_ABS_DPHI, PKR_TOL_REL_L2_DPHI = 0, 1
 
 # Every symbol include/pkr.h declares (checked by the tests).

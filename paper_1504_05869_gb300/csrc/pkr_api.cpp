@@ -799,9 +799,36 @@ int pkr_plan_import(pkr_plan* P, const pkr_plan* F)
         P->soff_next = 0.0;
         return PKR_OK;
     }
-    if (P->prob.precision == PKR_FP16 || P->prob.precision == PKR_FX64 ||
-        F->prob.precision == PKR_FX64)
-        return PKR_EINVAL;   // imports into binary16 or fixed point, or from fixed point: no
+    if (P->prob.precision == PKR_FP16 || F->prob.precision == PKR_FX64)
+        return PKR_EINVAL;   // imports into binary16, or from fixed point: no
+    const float* in_scale = F->prob.precision == PKR_FP16 ? F->h16sc + F->cur : nullptr;
+    if (P->prob.precision == PKR_FX64) {
+        // into fixed point: the exponent from the largest converted magnitude
+        // (both arrays start at it; the device rescale lowers it as needed)
+        unsigned long long mb = 0;
+        PKR_CK(cudaMemsetAsync(P->fxmax, 0, sizeof(unsigned long long), P->stream));
+        if (launch_absmax_shift(F->pop[F->cur], F->prob.precision, P->lat.Q, P->V, P->partials,
+                                in_scale, P->fxmax, P->stream) != 0)
+            return PKR_ECUDA;
+        PKR_CK(cudaMemcpyAsync(&mb, P->fxmax, sizeof(mb), cudaMemcpyDeviceToHost, P->stream));
+        PKR_CK(cudaStreamSynchronize(P->stream));
+        double m = 0.0;
+        std::memcpy(&m, &mb, sizeof(m));
+        const int Fx = fx_exponent(m);
+        const int F2[2] = {Fx, Fx};
+        PKR_CK(cudaMemcpyAsync(P->fxF, F2, sizeof(F2), cudaMemcpyHostToDevice, P->stream));
+        PKR_CK(cudaMemsetAsync(P->fxmax, 0, sizeof(unsigned long long), P->stream));
+        if (launch_convert_fx(F->pop[F->cur], F->prob.precision,
+                              static_cast<long long*>(P->pop[P->cur]), P->lat.Q, P->V,
+                              P->partials, in_scale, Fx, P->stream) != 0 ||
+            launch_make_source(P->Phi, P->scal + 5, 1.0, P->V, P->Phi, PKR_FP64, P->stream) != 0)
+            return PKR_ECUDA;
+        PKR_CK(cudaStreamSynchronize(P->stream));
+        P->launches = F->launches;
+        P->last_residual = F->last_residual;
+        P->soff_next = 0.0;
+        return PKR_OK;
+    }
     if (launch_convert_shift(F->pop[F->cur], F->prob.precision, P->pop[P->cur], P->prob.precision,
                              P->lat.Q, P->V, P->partials, P->stream, F->h16sc + F->cur) != 0 ||
         launch_make_source(P->Phi, P->scal + 5, 1.0, P->V, P->Phi, PKR_FP64, P->stream) != 0)
@@ -955,9 +982,9 @@ int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buf
         stages[nst] = PKR_FP16, switch_tol[nst++] = PKR_MIXED16_SWITCH_TOL;
         stages[nst] = PKR_FP32, switch_tol[nst++] = PKR_MIXED_SWITCH_TOL;
         stages[nst] = PKR_FP64, switch_tol[nst++] = p->tol;
-    } else if (p->precision == PKR_MIXED) {
+    } else if (p->precision == PKR_MIXED || p->precision == PKR_MIXED_FX64) {
         stages[nst] = PKR_FP32, switch_tol[nst++] = PKR_MIXED_SWITCH_TOL;
-        stages[nst] = PKR_FP64, switch_tol[nst++] = p->tol;
+        stages[nst] = p->precision == PKR_MIXED ? PKR_FP64 : PKR_FX64, switch_tol[nst++] = p->tol;
     } else {
         stages[nst] = p->precision, switch_tol[nst++] = p->tol;
     }

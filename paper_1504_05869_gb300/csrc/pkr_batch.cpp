@@ -368,11 +368,46 @@ int promote(pkr_ctx* C, Job* j)
         std::vector<double> shift(C->li.Q);
         for (int i = 0; i < C->li.Q; ++i) shift[i] = c * C->li.phi[i];
         if (cudaMemcpyAsync(C->d_scratch, shift.data(), shift.size() * 8, cudaMemcpyHostToDevice,
-                            C->stream) != cudaSuccess ||
-            launch_convert_shift(old_pop[cur], PKR_FP32, j->pop[cur], PKR_FP64, C->li.Q, j->V,
-                                 C->d_scratch, C->stream) != 0 ||
-            launch_make_source(j->Phi, C->d_mean, 1.0, j->V, j->Phi, PKR_FP64, C->stream) != 0 ||
-            cudaStreamSynchronize(C->stream) != cudaSuccess)
+                            C->stream) != cudaSuccess)
+            rc = PKR_ECUDA;
+        if (rc == PKR_OK && L1.prec == PKR_FX64) {
+            // into fixed point: exponent from the largest converted magnitude
+            if (!j->fx && cudaMallocAsync(&j->fx, 16, C->stream) != cudaSuccess) {
+                cudaGetLastError();
+                j->fx = nullptr;
+                rc = PKR_ECUDA;
+            }
+            unsigned long long* mb =
+                j->fx ? reinterpret_cast<unsigned long long*>(static_cast<char*>(j->fx) + 8)
+                      : nullptr;
+            unsigned long long hm = 0;
+            if (rc == PKR_OK &&
+                (cudaMemsetAsync(mb, 0, 8, C->stream) != cudaSuccess ||
+                 launch_absmax_shift(old_pop[cur], PKR_FP32, C->li.Q, j->V, C->d_scratch, nullptr,
+                                     mb, C->stream) != 0 ||
+                 cudaMemcpyAsync(&hm, mb, 8, cudaMemcpyDeviceToHost, C->stream) != cudaSuccess ||
+                 cudaStreamSynchronize(C->stream) != cudaSuccess))
+                rc = PKR_ECUDA;
+            if (rc == PKR_OK) {
+                double m = 0.0;
+                std::memcpy(&m, &hm, sizeof(m));
+                const int Fx = fx_exponent(m);
+                const int F2[2] = {Fx, Fx};
+                if (cudaMemcpyAsync(j->fx, F2, sizeof(F2), cudaMemcpyHostToDevice, C->stream) !=
+                        cudaSuccess ||
+                    cudaMemsetAsync(mb, 0, 8, C->stream) != cudaSuccess ||
+                    launch_convert_fx(old_pop[cur], PKR_FP32, static_cast<long long*>(j->pop[cur]),
+                                      C->li.Q, j->V, C->d_scratch, nullptr, Fx, C->stream) != 0)
+                    rc = PKR_ECUDA;
+            }
+        } else if (rc == PKR_OK &&
+                   launch_convert_shift(old_pop[cur], PKR_FP32, j->pop[cur], PKR_FP64, C->li.Q,
+                                        j->V, C->d_scratch, C->stream) != 0) {
+            rc = PKR_ECUDA;
+        }
+        if (rc == PKR_OK &&
+            (launch_make_source(j->Phi, C->d_mean, 1.0, j->V, j->Phi, PKR_FP64, C->stream) != 0 ||
+             cudaStreamSynchronize(C->stream) != cudaSuccess))
             rc = PKR_ECUDA;
     }
     if (rc == PKR_OK) {
@@ -684,7 +719,8 @@ int pkr_ctx_create(const pkr_ctx_config* cfg, void* stream, pkr_ctx** out)
     *out = nullptr;
     if (cfg->check_every < 1 || cfg->hbm_budget_bytes == 0) return PKR_EINVAL;
     if (cfg->precision != PKR_FP64 && cfg->precision != PKR_FP32 &&
-        cfg->precision != PKR_MIXED && cfg->precision != PKR_FX64)
+        cfg->precision != PKR_MIXED && cfg->precision != PKR_FX64 &&
+        cfg->precision != PKR_MIXED_FX64)
         return PKR_EINVAL;
     LatticeInfo li;
     int rc = build_lattice(cfg->lattice, cfg->order, &li);
@@ -699,7 +735,7 @@ int pkr_ctx_create(const pkr_ctx_config* cfg, void* stream, pkr_ctx** out)
     C->K = cfg->check_every;
     C->budget = cfg->hbm_budget_bytes;
     C->max_grids = cfg->max_grids > 0 ? cfg->max_grids : 4096;
-    C->mixed = cfg->precision == PKR_MIXED;
+    C->mixed = cfg->precision == PKR_MIXED || cfg->precision == PKR_MIXED_FX64;
     C->nlanes = C->mixed ? 2 : 1;
     bool ok = cudaGetDevice(&C->device) == cudaSuccess &&
               cudaDeviceGetAttribute(&C->nsm, cudaDevAttrMultiProcessorCount, C->device) ==
@@ -709,7 +745,8 @@ int pkr_ctx_create(const pkr_ctx_config* cfg, void* stream, pkr_ctx** out)
               cudaMalloc((void**)&C->d_mean, sizeof(double)) == cudaSuccess &&
               cudaMallocHost((void**)&C->h_flag, sizeof(int)) == cudaSuccess &&
               cudaMallocHost((void**)&C->h_mean, sizeof(double)) == cudaSuccess;
-    const int precs[2] = {C->mixed ? PKR_FP32 : cfg->precision, PKR_FP64};
+    const int precs[2] = {C->mixed ? PKR_FP32 : cfg->precision,
+                          cfg->precision == PKR_MIXED_FX64 ? PKR_FX64 : PKR_FP64};
     for (int ln = 0; ok && ln < C->nlanes; ++ln) ok = init_lane(C, C->lane[ln], precs[ln]);
     if (!ok) {
         cudaGetLastError();

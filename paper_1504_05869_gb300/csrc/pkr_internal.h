@@ -1,5 +1,6 @@
 // pkr_internal.h -- declarations shared by the library's translation units.
 #pragma once
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -152,6 +153,24 @@ int launch_convert(const void* in, int in_precision, void* out, int out_precisio
 // shift; shift: Q doubles in device memory).
 int launch_convert_shift(const void* in, int in_precision, void* out, int out_precision, int Q,
                          int64_t V, const double* shift, void* stream, const float* in_scale = nullptr);
+// Into 64-bit fixed point: max |in * in_scale - shift_i| over Q planes (as
+// binary64 bits, atomicMax into *out), and out = round((in * in_scale -
+// shift_i) 2^F).  in_scale: binary16 inputs only (device pointer).
+int launch_absmax_shift(const void* in, int in_precision, int Q, int64_t V, const double* shift,
+                        const float* in_scale, unsigned long long* out, void* stream);
+int launch_convert_fx(const void* in, int in_precision, long long* out, int Q, int64_t V,
+                      const double* shift, const float* in_scale, int F, void* stream);
+// Exponent of a fixed-point array whose largest magnitude is m: the largest
+// stored value lands in [2^51, 2^52).
+inline int fx_exponent(double m)
+{
+    int e = 0;
+    if (m > 0.0 && m < 1.0e300) {
+        std::frexp(m, &e);   // m in [2^(e-1), 2^e)
+        return 52 - e;
+    }
+    return 0;
+}
 // binary16 storage: after a step, set the scale of the array the next step
 // writes (sc[next]) from this step's max |p| (4x headroom), reset the max.
 int launch_h16_rescale(float* sc, unsigned int* pmax, int next, void* stream);

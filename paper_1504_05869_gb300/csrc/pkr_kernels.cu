@@ -247,6 +247,37 @@ __global__ void convert_shift_kernel(const TI* __restrict__ in, TO* __restrict__
         out[k] = (TO)(to_double(in[k]) * sc - sh[k / V]);
 }
 
+// max |in * scale - sh_i| over Q planes, as binary64 bits (atomicMax into *out).
+template <typename TI>
+__global__ void absmax_shift_kernel(const TI* __restrict__ in, int Q, int64_t V,
+                                    const double* __restrict__ sh,
+                                    const float* __restrict__ scale, unsigned long long* out)
+{
+    const int64_t n = (int64_t)Q * V;
+    const double sc = scale ? (double)*scale : 1.0;
+    double m = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
+        m = fmax(m, fabs(to_double(in[k]) * sc - sh[k / V]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// 64-bit fixed point: out = round((in * scale - sh_i) 2^F).
+template <typename TI>
+__global__ void convert_fx_kernel(const TI* __restrict__ in, long long* __restrict__ out, int Q,
+                                  int64_t V, const double* __restrict__ sh,
+                                  const float* __restrict__ scale, int F)
+{
+    const int64_t n = (int64_t)Q * V;
+    const double sc = scale ? (double)*scale : 1.0;
+    const double f = ldexp(1.0, F);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
+        out[k] = __double2ll_rn((to_double(in[k]) * sc - sh[k / V]) * f);
+}
+
 __global__ void h16_rescale_kernel(float* sc, unsigned int* pmax, int next)
 {
     const float m = __uint_as_float(*pmax);
@@ -453,6 +484,44 @@ int launch_finalize_check(const double* partials, int nblocks, double* out4, Run
 {
     finalize_check_kernel<<<1, kRedThreads, 0, (cudaStream_t)stream>>>(partials, nblocks, out4,
                                                                        ctl, tol, tol_kind, j);
+    return (int)cudaGetLastError();
+}
+
+int launch_absmax_shift(const void* in, int in_precision, int Q, int64_t V, const double* shift,
+                        const float* in_scale, unsigned long long* out, void* stream)
+{
+    const int blocks = 152 * 8;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (in_precision == PKR_FP64)
+        absmax_shift_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(in), Q, V,
+                                                            shift, nullptr, out);
+    else if (in_precision == PKR_FP32)
+        absmax_shift_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(in), Q, V,
+                                                           shift, nullptr, out);
+    else if (in_precision == kFP16 && in_scale)
+        absmax_shift_kernel<__half><<<blocks, 256, 0, st>>>(static_cast<const __half*>(in), Q, V,
+                                                            shift, in_scale, out);
+    else
+        return (int)cudaErrorInvalidValue;
+    return (int)cudaGetLastError();
+}
+
+int launch_convert_fx(const void* in, int in_precision, long long* out, int Q, int64_t V,
+                      const double* shift, const float* in_scale, int F, void* stream)
+{
+    const int blocks = 152 * 16;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (in_precision == PKR_FP64)
+        convert_fx_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(in), out, Q,
+                                                          V, shift, nullptr, F);
+    else if (in_precision == PKR_FP32)
+        convert_fx_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(in), out, Q, V,
+                                                         shift, nullptr, F);
+    else if (in_precision == kFP16 && in_scale)
+        convert_fx_kernel<__half><<<blocks, 256, 0, st>>>(static_cast<const __half*>(in), out, Q,
+                                                          V, shift, in_scale, F);
+    else
+        return (int)cudaErrorInvalidValue;
     return (int)cudaGetLastError();
 }
 

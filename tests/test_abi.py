@@ -102,6 +102,7 @@ def test_invalid_problems_rejected_before_any_gpu_work(pkr):
     assert _create(pkr, lattice="D2Q169", order=7)[0] == -1   # 2D set on a 3D grid
     assert _create(pkr, shape=(0, 8, 8))[0] == -1
     assert _create(pkr, max_sweeps=0)[0] == -1
+    assert _create(pkr, precision="mixed_fx64")[0] == -1  # ladders: pkr_solve and contexts
     p = pkr.problem("D3Q111", (8, 8, 8), 5, tau_lb=1.0)
     p.tol_kind = 7
     h = ctypes.c_void_p()
@@ -170,6 +171,7 @@ def test_context_config_validation(pk_cfg=None):
     assert create(hbm_budget_bytes=0) == -1
     assert create(precision=7) == -1
     assert create(precision=3) == -1      # binary16 storage: pkr_solve only
+    assert create(precision=8) == -1
     assert create(variant=99) == -1
     assert create(order=7) == -1
     assert create(lattice=42) == -1

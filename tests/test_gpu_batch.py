@@ -153,14 +153,15 @@ MIXED_JOBS = [((12, 10, 14), 1.3, 1e-10, 4), ((9, 7, 13), 2.0, 1e-9, 5),
               ((20, 11, 8), 3.0, 1e-6, 8)]
 
 
-@pytest.mark.parametrize("threaded", [False, True])
-def test_mixed_batch_reaches_binary64_tolerances(pk, threaded):
+@pytest.mark.parametrize("precision,threaded", [("mixed", False), ("mixed", True),
+                                                ("mixed_fx64", False)])
+def test_mixed_batch_reaches_binary64_tolerances(pk, precision, threaded):
     """MIXED context: every request meets its tolerance (below what binary32
     can reach for all but the last), and lands as close to the scheme's exact
     fixed point as that tolerance allows (error ~ residual / spectral gap;
     the gap of these grids is >= 0.05, so 50 x tol bounds it, plus the
     binary32 floor for the request that finishes in binary32)."""
-    res, info = _run_ctx(pk, MIXED_JOBS, "mixed", threaded=threaded)
+    res, info = _run_ctx(pk, MIXED_JOBS, precision, threaded=threaded)
     assert info["finished"] == len(MIXED_JOBS) and info["bytes_in_use"] == 0
     for rho, got, rc, st, tau, tol in res:
         assert rc == 0, rc
@@ -170,9 +171,10 @@ def test_mixed_batch_reaches_binary64_tolerances(pk, threaded):
         assert _rel(got, fx) <= 50 * tol + (2e-5 if tol >= 1e-6 else 0.0), (rho.shape, _rel(got, fx))
 
 
-def test_mixed_same_result_alone_and_in_mix(pk):
-    alone, _ = _run_ctx(pk, MIXED_JOBS[:1], "mixed")
-    mixed, _ = _run_ctx(pk, MIXED_JOBS[1:3] + MIXED_JOBS[:1] + MIXED_JOBS[3:], "mixed")
+@pytest.mark.parametrize("precision", ["mixed", "mixed_fx64"])
+def test_mixed_same_result_alone_and_in_mix(pk, precision):
+    alone, _ = _run_ctx(pk, MIXED_JOBS[:1], precision)
+    mixed, _ = _run_ctx(pk, MIXED_JOBS[1:3] + MIXED_JOBS[:1] + MIXED_JOBS[3:], precision)
     a, b = alone[0], mixed[2]
     assert a[3]["sweeps"] == b[3]["sweeps"]
     assert np.array_equal(a[1], b[1])

@@ -357,6 +357,19 @@ def test_fixed_steps_fp16(pk, lattice, order, shape, tau):
     assert _rel(got, ref) < 5e-3, _rel(got, ref)
 
 
+def test_mixed_fx64_ladder_reaches_binary64_fixed_point(pk):
+    """binary32 steps, then 64-bit fixed point from the converted state (its
+    exponent set from the largest converted magnitude)."""
+    shape = (12, 10, 14)
+    rho, _ = stiff_source(shape, count=6, sigma=1.5, seed=16)
+    star = oracle.solve(rho, "D3Q111", 5, tau_lb=1.3, tol=1e-15, tol_kind=1,
+                        check_every=8, max_steps=400000).phi
+    got, rc, st = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-12, precision="mixed_fx64",
+                             max_sweeps=400000)
+    assert rc == 0 and st["residual"] < 1e-12
+    assert _rel(got, star) < 5e-9
+
+
 def test_mixed16_ladder_reaches_binary64_fixed_point(pk):
     shape = (12, 10, 14)
     rho, _ = stiff_source(shape, count=6, sigma=1.5, seed=19)
