@@ -235,7 +235,18 @@ __device__ __forceinline__ bool plain_path(int emax) { return emax == 0x7ff || e
 template <int GB>
 __device__ __forceinline__ double fixed_value(long long acc, int emax)
 {
-    return (double)acc * __longlong_as_double((long long)(emax - 52 - GB) << 52);
+    // acc x 2^(emax - 1075 - GB): the power of two is added to the exponent
+    // field of the converted value on the integer pipe (the binary64 pipe is
+    // the scarce one).  emax >= 64 here (plain_path), so a non-zero result is
+    // normal; past the binary64 range it is +-inf, as the product would be.
+    const double d = (double)acc;
+    const long long b = __double_as_longlong(d);
+    const int k = emax - 1075 - GB;
+    const int be = (int)((b >> 52) & 0x7ff) + k;
+    if (acc == 0) return d;
+    if (be >= 0x7ff) return acc > 0 ? __longlong_as_double(0x7ff0000000000000ll)
+                                    : __longlong_as_double((long long)0xfff0000000000000ull);
+    return __longlong_as_double(b + ((long long)k << 52));
 }
 
 template <int Q>
@@ -345,7 +356,12 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
         }
     }
     const int nbytes = (valid && !zero_in) ? (int)sizeof(T) : 0;
-    const R Sx = valid ? (R)((double)tg.S[s] + tg.soff) : R(0);
+    // the source offset (mass correction) is used by binary32 storage only
+    R Sx = R(0);
+    if (valid) {
+        if constexpr (std::is_same<T, float>::value) Sx = (R)((double)tg.S[s] + tg.soff);
+        else Sx = (R)tg.S[s];
+    }
 
     static_for<0, G>([&](auto GI) {
         constexpr int g = decltype(GI)::value;
