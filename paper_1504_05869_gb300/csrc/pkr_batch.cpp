@@ -26,6 +26,7 @@
 #include <mutex>
 #include <new>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "pkr_internal.h"
@@ -108,7 +109,9 @@ struct Job {
     void* pop[2] = {nullptr, nullptr};   // populations in the precision of the job's lane
     void* S = nullptr;                   // source, same precision
     double* Phi = nullptr;               // density (binary64)
-    void* fx = nullptr;                  // fixed-point lanes: int F[2], then the OR bound (u64)
+    void* fx = nullptr;                  // 16 B of per-grid device state: fixed-point lanes
+                                         // int F[2], then the OR bound (u64); binary32
+                                         // lanes the source offset (double)
     size_t bytes = 0;                    // bytes counted against the budget (reservation)
     int64_t V = 0;
     int ntiles = 0;
@@ -131,7 +134,7 @@ struct Lane {
     double* d_tile_partials = nullptr;
     int64_t tiles_cap = 0;
     double* d_res = nullptr;
-    double* h_res = nullptr;   // pinned, 3 per grid slot
+    double* h_res = nullptr;   // pinned, 4 per grid slot
     cudaGraphExec_t graph = nullptr;
     long long step = 0;
     bool dirty = true;
@@ -184,6 +187,7 @@ void fill_grid(unsigned char* dst, const Job* j, const LatticeInfo& li, int tile
     g.small = j->small;
     g.tile_begin = tile_begin;
     g.join = j->join;
+    if constexpr (std::is_same<R, float>::value) g.soff = static_cast<double*>(j->fx);
     if (j->fx) {
         g.fxF = static_cast<int*>(j->fx);
         g.fxmax = reinterpret_cast<unsigned long long*>(static_cast<char*>(j->fx) + 8);
@@ -297,6 +301,15 @@ int admit(pkr_ctx* C, Job* j)
     int rc = make_job_source(C, j, rd, 0);
     if (rc != PKR_OK) return rc;
     if (cudaMemsetAsync(j->Phi, 0, (size_t)j->V * 8, C->stream) != cudaSuccess) return PKR_ECUDA;
+    if (C->lane[0].prec == PKR_FP32) {
+        // the source offset of the binary32 mass correction (0 until a check)
+        if (cudaMallocAsync(&j->fx, 16, C->stream) != cudaSuccess) {
+            cudaGetLastError();
+            j->fx = nullptr;
+            return PKR_ENOMEM;
+        }
+        if (cudaMemsetAsync(j->fx, 0, 16, C->stream) != cudaSuccess) return PKR_ECUDA;
+    }
     if (C->lane[0].prec == PKR_FX64) {
         // exponent of the first write (the step from zero stores chi_i S): its
         // largest value lands near 2^52, as for a plan
@@ -446,7 +459,7 @@ int rebuild(pkr_ctx* C, Lane& L)
         if (L.d_tile_partials) cudaFreeAsync(L.d_tile_partials, C->stream);
         L.d_tile_partials = nullptr;
         int64_t cap = tiles + tiles / 4 + 1024;
-        if (cudaMallocAsync((void**)&L.d_tile_partials, (size_t)cap * 3 * sizeof(double),
+        if (cudaMallocAsync((void**)&L.d_tile_partials, (size_t)cap * 4 * sizeof(double),
                             C->stream) != cudaSuccess) {
             L.tiles_cap = 0;
             return PKR_ENOMEM;
@@ -490,7 +503,7 @@ int enqueue_window(pkr_ctx* C, Lane& L)
             return PKR_ECUDA;
     }
     if (launch_batch_reduce(L.d_state, C->max_grids, L.grid_stride, C->stream) != 0 ||
-        cudaMemcpyAsync(L.h_res, L.d_res, (size_t)C->max_grids * 3 * sizeof(double),
+        cudaMemcpyAsync(L.h_res, L.d_res, (size_t)C->max_grids * 4 * sizeof(double),
                         cudaMemcpyDeviceToHost, C->stream) != cudaSuccess)
         return PKR_ECUDA;
     return PKR_OK;
@@ -528,7 +541,7 @@ int retire(pkr_ctx* C, int ln, long long step0)
         const long long age_end = L.step - 1 - j->join;    // age of the window's last step
         C->site_updates += (double)j->V * (double)(L.step - (step0 > j->join ? step0 : j->join));
         const bool checked = age_end >= 1;
-        const double* r = L.h_res + 3 * k;
+        const double* r = L.h_res + 4 * k;
         const double res = r[j->prob.tol_kind == PKR_TOL_MAX_ABS_DPHI ? 0 : 1];
         const double tol = j->prob.tol;
         int status = PKR_EBUSY;
@@ -690,9 +703,9 @@ bool init_lane(pkr_ctx* C, Lane& L, int prec)
     std::memset(&L.h_state, 0, sizeof(BatchState));
     return cudaMalloc((void**)&L.d_state, sizeof(BatchState)) == cudaSuccess &&
            cudaMalloc((void**)&L.d_grids, (size_t)C->max_grids * L.grid_stride) == cudaSuccess &&
-           cudaMalloc((void**)&L.d_res, (size_t)C->max_grids * 3 * sizeof(double)) ==
+           cudaMalloc((void**)&L.d_res, (size_t)C->max_grids * 4 * sizeof(double)) ==
                cudaSuccess &&
-           cudaMallocHost((void**)&L.h_res, (size_t)C->max_grids * 3 * sizeof(double)) ==
+           cudaMallocHost((void**)&L.h_res, (size_t)C->max_grids * 4 * sizeof(double)) ==
                cudaSuccess &&
            cudaMemcpy(L.d_state, &L.h_state, sizeof(BatchState), cudaMemcpyHostToDevice) ==
                cudaSuccess;

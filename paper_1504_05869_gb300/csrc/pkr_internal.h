@@ -61,6 +61,9 @@ struct BatchGrid {
     int* fxF;
     unsigned long long* fxmax;
     long long cfx;
+    // binary32 storage only (device memory of the grid): source offset that
+    // removes the measured mass, written at a check, used by the next step
+    double* soff;
     Coefs<R> c;
 };
 
@@ -68,8 +71,8 @@ struct BatchGrid {
 // stays valid while grids join and retire.
 struct BatchState {
     const void* grids;     // BatchGrid<R>[ngrids], sorted by tile_begin
-    double* tile_partials; // 3 doubles per batch-wide tile (check steps)
-    double* grid_res;      // 3 doubles per grid (after the per-grid reduction)
+    double* tile_partials; // 4 doubles per batch-wide tile (check steps)
+    double* grid_res;      // 4 doubles per grid (after the per-grid reduction)
     long long step;        // batch step counter (launch index)
     int ngrids;
     int ntiles;

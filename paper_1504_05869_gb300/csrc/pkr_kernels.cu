@@ -193,37 +193,48 @@ batch_reduce_kernel(const BatchState* st, int stride_bytes)
                        ? *reinterpret_cast<const int*>(base + (size_t)(g + 1) * stride_bytes + off)
                        : st->ntiles;
     const double* p = st->tile_partials;
-    __shared__ double s0[kRedThreads / 32], s1[kRedThreads / 32], s2[kRedThreads / 32];
-    double d2 = 0.0, n2 = 0.0, mx = 0.0;
+    __shared__ double s0[kRedThreads / 32], s1[kRedThreads / 32], s2[kRedThreads / 32],
+        s3[kRedThreads / 32];
+    double d2 = 0.0, n2 = 0.0, mx = 0.0, ms = 0.0;
     for (int t = tb + (int)threadIdx.x; t < te; t += kRedThreads) {
-        d2 += p[3 * (int64_t)t + 0];
-        n2 += p[3 * (int64_t)t + 1];
-        mx = fmax(mx, p[3 * (int64_t)t + 2]);
+        d2 += p[4 * (int64_t)t + 0];
+        n2 += p[4 * (int64_t)t + 1];
+        mx = fmax(mx, p[4 * (int64_t)t + 2]);
+        ms += p[4 * (int64_t)t + 3];
     }
     d2 = warp_sum(d2);
     n2 = warp_sum(n2);
     mx = warp_max(mx);
+    ms = warp_sum(ms);
     if ((threadIdx.x & 31) == 0) {
         s0[threadIdx.x >> 5] = d2;
         s1[threadIdx.x >> 5] = n2;
         s2[threadIdx.x >> 5] = mx;
+        s3[threadIdx.x >> 5] = ms;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0, c = 0.0;
+        double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
         for (int k = 0; k < kRedThreads / 32; ++k) {
             a += s0[k];
             b += s1[k];
             c = fmax(c, s2[k]);
+            d += s3[k];
         }
-        double* out = st->grid_res + 3 * g;
+        double* out = st->grid_res + 4 * g;
         out[0] = c;
         out[1] = (b > 0.0) ? sqrt(a) / sqrt(b) : (a == 0.0 ? 0.0 : INFINITY);
         out[2] = sqrt(b);
+        out[3] = d;
         if (!(a == a) || !(b == b)) {
             out[0] = NAN;
             out[1] = NAN;
         }
+        // binary32 grids: the next step removes the measured mass through
+        // its source (sum_i chi_i = 1, so -mass / V per site removes it)
+        const BatchGrid<double>& gd =
+            *reinterpret_cast<const BatchGrid<double>*>(base + (size_t)g * stride_bytes);
+        if (gd.soff) *gd.soff = isfinite(d) ? -d / (double)gd.V : 0.0;
     }
 }
 

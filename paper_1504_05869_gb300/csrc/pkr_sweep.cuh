@@ -588,8 +588,9 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
 // since it joined) picks its buffers and its own residual schedule: it writes
 // Phi when (age + 2) % K == 0 and checks when (age + 1) % K == 0 (age >= 1),
 // so a grid's trajectory and stopping step do not depend on what else is in
-// the batch.  On check steps each tile leaves its three partial sums in
-// tile_partials; pkr_batch_reduce sums them per grid in a fixed order.
+// the batch.  On check steps each tile leaves its four partial sums in
+// tile_partials (with the sum of Phi); pkr_batch_reduce sums them per grid in
+// a fixed order.
 // ---------------------------------------------------------------------------
 template <class L, typename T, int G_, int TILES_>
 __global__ void __launch_bounds__(G_ * TILES_ * 32)
@@ -631,9 +632,11 @@ sweep_batch_kernel(BatchState* st, int K)
         if (age >= 1 && (age + 1) % K == 0) mode = kCheck;
         else if (zero_in || (age + 2) % K == 0) mode = kWritePhi;
         constexpr bool fx = std::is_same<T, long long>::value;
+        // binary32: the step after a check removes the mass that check measured
+        const double soff = (gd.soff && age >= 1 && age % K == 0) ? *gd.soff : 0.0;
         const TileGrid<T> tg{static_cast<const T*>(gd.pop[cur]), static_cast<T*>(gd.pop[cur ^ 1]),
                              static_cast<const typename SrcType<T>::type*>(gd.S), gd.Phi, gd.V,
-                             gd.nx, gd.ny, gd.nz, gd.small, 0.0, fx ? gd.fxF[cur] : 0,
+                             gd.nx, gd.ny, gd.nz, gd.small, soff, fx ? gd.fxF[cur] : 0,
                              fx ? gd.fxF[cur ^ 1] : 0, fx ? gd.cfx : 0};
         double d2 = 0.0, n2 = 0.0, mx = 0.0, ms = 0.0;
         unsigned long long fxm = 0ull;
@@ -650,11 +653,13 @@ sweep_batch_kernel(BatchState* st, int K)
                 d2 += __shfl_down_sync(0xffffffffu, d2, o);
                 n2 += __shfl_down_sync(0xffffffffu, n2, o);
                 mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+                ms += __shfl_down_sync(0xffffffffu, ms, o);
             }
             if (lane == 0) {
-                tpart[3 * (int64_t)tile + 0] = d2;
-                tpart[3 * (int64_t)tile + 1] = n2;
-                tpart[3 * (int64_t)tile + 2] = mx;
+                tpart[4 * (int64_t)tile + 0] = d2;
+                tpart[4 * (int64_t)tile + 1] = n2;
+                tpart[4 * (int64_t)tile + 2] = mx;
+                tpart[4 * (int64_t)tile + 3] = ms;
             }
         }
     }

@@ -195,3 +195,29 @@ def test_mixed_budget_reserves_both_states(pk):
     with pytest.raises(pk.PkrError) as e:
         _run_ctx(pk, jobs[:1], "mixed", budget=one - 1)
     assert e.value.status == -2
+
+
+def test_fp32_batch_mass_drift_is_removed(pk):
+    """Long binary32 run in a context: each grid's measured mass is removed
+    through the source of the step after each check, so the mass stays at
+    its exact value 0 (to binary32 noise) and Phi stays within 2e-6 of the
+    scheme's fixed point instead of random-walking away from it."""
+    import torch
+    import pins
+    shape = (16, 16, 16)
+    rho, _ = stiff_source(shape, count=4, sigma=2.0, seed=17)
+    lat = oracle.lattice("D3Q111", 5)
+    tau = 15.0
+    S, _ = oracle.source(rho, lat, tau)
+    star = pins.fixed_point(S, lat.vel, lat.phi, lat.chi, 1 / tau)
+    ctx = pk.Context("D3Q111", 5, precision="fp32", check_every=32, hbm_budget_bytes=10 ** 9)
+    r = torch.from_numpy(rho).cuda()
+    phi = torch.zeros_like(r)
+    t = ctx.submit(r, phi, tau_lb=tau, tol=0.0, max_sweeps=6000)
+    ctx.run()
+    rc, st = ctx.poll(t)
+    ctx.close()
+    assert rc == 0 and st["sweeps"] >= 6000
+    got = phi.cpu().numpy()
+    assert abs(got.mean()) < 1e-7 * np.sqrt((got ** 2).mean())
+    assert _rel(got, star) < 2e-6
