@@ -337,7 +337,9 @@ def run(args):
                        "order": ORDER, "knudsen": None if TAU > 0 else KN, "tau_lb": tau,
                        "sweeps_per_step": SWEEPS_PER_STEP, "residual_check": "rel_l2 fp64",
                        "kernel_variant": variant,
-                       "l2": "inputs larger than L2 (2 x 14.9 GB populations)",
+                       "l2": (f"inputs larger than L2 (2 x {Q * V * esize / 1e9:.2f} GB populations)"
+                              if Q * V * esize > 129e6 else
+                              f"populations ({2 * Q * V * esize / 1e6:.0f} MB) fit in L2"),
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs": V * bytes_site * sweeps * world / (dev_ms * 1e-3) / 1e9,
             "roofline": roofline,

@@ -170,54 +170,78 @@ __device__ __forceinline__ float lds_f32(uint32_t addr)
     return v;
 }
 
-// One term of the fixed-point density: the value rounded to the unit
-// 2^(emax - 1075 - GB), sign applied.
+// One term of the fixed-point density at twice its resolution: t = floor(2y)
+// for y = v / 2^(emax - 1075 - GB), the mantissa shifted right as a magnitude
+// and the sign applied by complement afterwards (for arithmetic shifts
+// ~(x >> r) == (~x) >> r, so a negative term becomes floor(2y - 2^-r), which
+// moves only exact ties).  floor((t + 1) / 2) = (t + (t & 1)) / 2 is then y
+// rounded to the nearest integer, ties away from zero.  A shift of 54 + GB or
+// more (zero, subnormal or negligible values) leaves 0 or -1, i.e. a rounded 0.
 template <int GB>
-__device__ __forceinline__ long long fixed_term(double v, int emax)
+__device__ __forceinline__ long long fixed_term2(double v, int emax)
 {
     const long long b = __double_as_longlong(v);
-    const int e = (int)((b >> 52) & 0x7ff);
-    const long long m = e ? (((b & 0xfffffffffffffll) | (1ll << 52)) << GB) : 0ll;
-    const int rs = emax - e;
-    const long long t = rs < 63 ? ((m + ((1ll << rs) >> 1)) >> rs) : 0ll;
-    return b < 0 ? -t : t;
+    const int hi = (int)(b >> 32);
+    const int e = (hi >> 20) & 0x7ff;
+    const unsigned long long m =
+        ((unsigned long long)(b & 0xfffffffffffffll) | (1ull << 52)) << (GB + 1);
+    // PTX shr.b64 clamps shift amounts above 64 to 64 (result 0): no min needed
+    unsigned long long r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(m), "r"(emax - e));
+    return (long long)r ^ (long long)(hi >> 31);
 }
 
 // Largest exponent among N staged binary64 values (stride 256 B).
 template <int N>
 __device__ __forceinline__ int max_exponent(uint32_t col)
 {
-    int h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+    int h0 = 0, h1 = 0;
 #pragma unroll 2
     for (int k = 0; k + 3 < N; k += 4) {
-        h0 = max(h0, lds_hi32(col + (k + 0) * 256) & 0x7fffffff);
-        h1 = max(h1, lds_hi32(col + (k + 1) * 256) & 0x7fffffff);
-        h2 = max(h2, lds_hi32(col + (k + 2) * 256) & 0x7fffffff);
-        h3 = max(h3, lds_hi32(col + (k + 3) * 256) & 0x7fffffff);
+        h0 = __vimax3_s32(h0, lds_hi32(col + (k + 0) * 256) & 0x7fffffff,
+                          lds_hi32(col + (k + 1) * 256) & 0x7fffffff);
+        h1 = __vimax3_s32(h1, lds_hi32(col + (k + 2) * 256) & 0x7fffffff,
+                          lds_hi32(col + (k + 3) * 256) & 0x7fffffff);
     }
 #pragma unroll
     for (int k = N - N % 4; k < N; ++k) h0 = max(h0, lds_hi32(col + k * 256) & 0x7fffffff);
-    return max(max(h0, h1), max(h2, h3)) >> 20;
+    return max(h0, h1) >> 20;
 }
 
-// Fixed-point sum of N staged binary64 values aligned to emax (GB guard bits).
+// Fixed-point sum of N staged binary64 values aligned to emax (GB guard bits):
+// the sum of the terms rounded to the unit, kept as four partial sums (term k
+// in partial k mod 4) of the doubled terms t_k and of their low bits (sum of
+// rounded terms = (sum t_k + sum (t_k & 1)) / 2, exact, and even per partial).
+// |t_k| < 2^(54 + GB), so a partial of fewer than 2^(9 - GB) terms cannot
+// overflow; with GB = 10 - ceil(log2 Q) that holds for every N <= Q.
 template <int GB, int N>
 __device__ __forceinline__ long long fixed_sum(uint32_t col, int emax)
 {
     constexpr int U = 8;
-    long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    static_assert((N + 3) / 4 < (1 << (9 - GB)), "fixed-point partial may overflow");
+    long long a[4] = {0, 0, 0, 0};
+    int p[4] = {0, 0, 0, 0};
     for (int k = 0; k + U - 1 < N; k += U) {
         double v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) v[u] = lds_f64(col + (k + u) * 256);
-        a0 += fixed_term<GB>(v[0], emax) + fixed_term<GB>(v[4], emax);
-        a1 += fixed_term<GB>(v[1], emax) + fixed_term<GB>(v[5], emax);
-        a2 += fixed_term<GB>(v[2], emax) + fixed_term<GB>(v[6], emax);
-        a3 += fixed_term<GB>(v[3], emax) + fixed_term<GB>(v[7], emax);
+        long long t[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) t[u] = fixed_term2<GB>(v[u], emax);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[u] += t[u] + t[u + 4];
+            p[u] += (int)(t[u] & 1) + (int)(t[u + 4] & 1);
+        }
     }
 #pragma unroll
-    for (int k = N - N % U; k < N; ++k) a0 += fixed_term<GB>(lds_f64(col + k * 256), emax);
-    return (a0 + a1) + (a2 + a3);
+    for (int k = N - N % U; k < N; ++k) {
+        const long long t = fixed_term2<GB>(lds_f64(col + k * 256), emax);
+        a[k % 4] += t;
+        p[k % 4] += (int)(t & 1);
+    }
+    return ((a[0] + p[0]) >> 1) + ((a[1] + p[1]) >> 1) + ((a[2] + p[2]) >> 1) +
+           ((a[3] + p[3]) >> 1);
 }
 
 template <int N>
