@@ -65,6 +65,16 @@ __device__ __forceinline__ int wrap_near(int c, int n)
     c = c < 0 ? c + n : c;
     return c >= n ? c - n : c;
 }
+// c - D wrapped into [0, n) for c in [0, n) and |D| <= n: only one side can
+// be crossed, and which one is known at compile time.
+template <int D>
+__device__ __forceinline__ int wrap_off(int c, int n)
+{
+    const int v = c - D;
+    if constexpr (D > 0) return v < 0 ? v + n : v;
+    else if constexpr (D < 0) return v >= n ? v - n : v;
+    else return v;
+}
 __device__ __forceinline__ int wrap_any(int c, int n)
 {
     int r = c % n;
@@ -362,22 +372,25 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
     const int64_t s64 = (int64_t)tile * 32 + lane;
     const bool valid = s64 < V;
     const int s = valid ? (int)s64 : 0;
-    const int x = s % nx;
-    const int r = s / nx;
-    const int y = r % ny;
-    const int z = r / ny;
+    const int r = (int)((unsigned)s / (unsigned)nx);
+    const int x = s - r * nx;
+    const int z = (int)((unsigned)r / (unsigned)ny);
+    const int y = r - z * ny;
     int xs[W], yo[W], zo[W];
+    if (tg.small) {
 #pragma unroll
-    for (int d = -RC; d <= RC; ++d) {
-        if (tg.small) {
+        for (int d = -RC; d <= RC; ++d) {
             xs[d + RC] = wrap_any(x - d, nx);
             yo[d + RC] = wrap_any(y - d, ny) * nx;
             zo[d + RC] = wrap_any(z - d, nz) * nxy;
-        } else {
-            xs[d + RC] = wrap_near(x - d, nx);
-            yo[d + RC] = wrap_near(y - d, ny) * nx;
-            zo[d + RC] = wrap_near(z - d, nz) * nxy;
         }
+    } else {
+        static_for<0, W>([&](auto DI) {
+            constexpr int d = decltype(DI)::value - RC;
+            xs[d + RC] = wrap_off<d>(x, nx);
+            yo[d + RC] = wrap_off<d>(y, ny) * nx;
+            zo[d + RC] = wrap_off<d>(z, nz) * nxy;
+        });
     }
     const int nbytes = (valid && !zero_in) ? (int)sizeof(T) : 0;
     // the source offset (mass correction) is used by binary32 storage only
