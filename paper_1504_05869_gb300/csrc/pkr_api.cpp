@@ -67,11 +67,10 @@ int variant_count(int lattice)
 }
 
 // Default geometry per lattice, from timing every variant on GB300 at 256^3
-// (D3Q111: (2,2) fastest in binary64, 2.15 GLUPS, and binary32, 5.57 GLUPS;
+// (D3Q111: (2,2) fastest in binary64, 2.52 GLUPS, and binary32, 5.57 GLUPS;
 // D3Q19: the two variants within 0.2 %).  Index into the lattice's variant
 // list {(G,TILES)} = {(1,2),(2,1),(2,2),(3,1),(3,2),(4,1)} for Q > 64, else
-// {(1,2),(1,4)}.
-// Default geometry: 2 velocity groups x 2 tiles for the large sets; on grids
+// {(1,2),(1,4)}: 2 velocity groups x 2 tiles for the large sets; on grids
 // with few tiles per SM, 4 groups x 1 tile (more warps share each tile, so
 // each step's chain is shorter).  All geometries give the same binary64 result.
 int default_variant(int lattice, int precision, int64_t V, int nsm)
