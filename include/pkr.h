@@ -29,6 +29,10 @@
  *     allocates and frees it in pkr_plan_destroy.
  *   - stream: a cudaStream_t passed as void*; NULL means the legacy default
  *     stream.  Calls that return results synchronise that stream.
+ *   - A NULL handle, or a NULL pointer where one is required, is refused
+ *     with PKR_EINVAL before any device work; pkr_plan_destroy(NULL) and
+ *     pkr_ctx_destroy(NULL) are no-ops returning PKR_OK.  Pointers an entry
+ *     point marks "may be NULL" are optional outputs.
  */
 #ifndef PKR_H
 #define PKR_H

@@ -197,3 +197,42 @@ def test_site_count_limits_rejected_on_the_host(pkr):
     out = (ctypes.c_double * 3)()
     for V in (0, -5, 2 ** 31):
         assert pkr._pkr.pkr_residual_noalloc(dummy, dummy, V, out, None) == -1
+
+
+def test_null_handles_and_pointers_rejected(pkr):
+    """Every entry point that takes a handle or an output pointer refuses NULL
+    with PKR_EINVAL before any device work; destroying NULL is a no-op
+    (PKR_OK); the handle queries return their empty values."""
+    L = pkr._pkr
+    st = L.pkr_stats()
+    dummy = ctypes.c_void_p(16)                     # never dereferenced: refused first
+    p = pkr.problem("D3Q111", (8, 8, 8), 5, tau_lb=1.0)
+    assert L.pkr_plan_create(ctypes.byref(p), None, None) == -1
+    assert L.pkr_plan_create(None, None, ctypes.byref(ctypes.c_void_p())) == -1
+    assert L.pkr_plan_destroy(None) == 0
+    assert L.pkr_plan_load_source(None, dummy, 0) == -1
+    assert L.pkr_plan_run(None, 1, 0.0, 0, 1, ctypes.byref(st)) == -1
+    assert L.pkr_plan_sweeps(None, 1) == -1
+    assert L.pkr_plan_phi(None, dummy, 0) == -1
+    assert L.pkr_plan_autotune(None, 1, None, None) == -1
+    assert L.pkr_plan_import(None, None) == -1
+    assert L.pkr_plan_steps(None) == 0
+    assert L.pkr_plan_populations(None) is None
+    assert L.pkr_solve(None, dummy, dummy, 0, ctypes.byref(st), None) == -1
+    assert L.pkr_solve(ctypes.byref(p), None, dummy, 0, ctypes.byref(st), None) == -1
+    assert L.pkr_solve(ctypes.byref(p), dummy, None, 0, ctypes.byref(st), None) == -1
+    assert L.pkr_plan_bytes(ctypes.byref(p), None) == -1
+    assert L.pkr_tau_from_knudsen(pkr.LATTICES["D3Q111"], 0.2, None, None) == -1
+    out = (ctypes.c_double * 3)()
+    assert L.pkr_residual_noalloc(None, dummy, 8, out, None) == -1
+    assert L.pkr_residual_noalloc(dummy, dummy, 8, None, None) == -1
+    cfg = pkr.pkr_ctx_config()
+    assert L.pkr_ctx_create(None, None, ctypes.byref(ctypes.c_void_p())) == -1
+    assert L.pkr_ctx_create(ctypes.byref(cfg), None, None) == -1
+    ticket = ctypes.c_uint64()
+    assert L.pkr_submit(None, ctypes.byref(p), dummy, dummy, 0, ctypes.byref(ticket)) == -1
+    assert L.pkr_poll(None, 0, ctypes.byref(st)) == -1
+    assert L.pkr_ctx_wait(None, 0, ctypes.byref(st)) == -1
+    assert L.pkr_ctx_run(None, 1) == -1
+    assert L.pkr_ctx_info(None, None, None, None, None, None) == -1
+    assert L.pkr_ctx_destroy(None) == 0
