@@ -280,7 +280,8 @@ int make_job_source(pkr_ctx* C, Job* j, const double* rd, int ln)
 }
 
 // Allocate and prepare a request in lane 0 (context stream; caller holds
-// the lock).  Returns PKR_OK, PKR_ENOMEM (try later) or a final error status.
+// the lock).  Returns PKR_OK, PKR_ENOMEM (try later; the request then holds no
+// memory and no share of the budget) or a final error status.
 int admit(pkr_ctx* C, Job* j)
 {
     if (!alloc_lane_state(C, j, 0)) return PKR_ENOMEM;
@@ -306,6 +307,7 @@ int admit(pkr_ctx* C, Job* j)
         if (cudaMallocAsync(&j->fx, 16, C->stream) != cudaSuccess) {
             cudaGetLastError();
             j->fx = nullptr;
+            free_job_memory(C, j);   // the request stays queued: hold nothing
             return PKR_ENOMEM;
         }
         if (cudaMemsetAsync(j->fx, 0, 16, C->stream) != cudaSuccess) return PKR_ECUDA;
@@ -315,6 +317,8 @@ int admit(pkr_ctx* C, Job* j)
         // largest value lands near 2^52, as for a plan
         if (cudaMallocAsync(&j->fx, 16, C->stream) != cudaSuccess) {
             cudaGetLastError();
+            j->fx = nullptr;
+            free_job_memory(C, j);   // the request stays queued: hold nothing
             return PKR_ENOMEM;
         }
         unsigned long long* mb = reinterpret_cast<unsigned long long*>(static_cast<char*>(j->fx) + 8);
