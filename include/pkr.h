@@ -348,6 +348,14 @@ int pkr_ctx_run(pkr_ctx *ctx, int64_t max_windows);
  * pkr_poll does. */
 int pkr_ctx_wait(pkr_ctx *ctx, uint64_t ticket, pkr_stats *stats);
 
+/* Forget a finished request: its ticket becomes invalid and the context's
+ * record of it (status and stats) is freed.  Long-running contexts call this
+ * once a request's result has been read, so that their bookkeeping stays
+ * bounded.  Errors: PKR_EINVAL (NULL context or unknown ticket), PKR_EBUSY
+ * (the request is still queued or running, or another thread is waiting on
+ * it in pkr_ctx_wait). */
+int pkr_ctx_release(pkr_ctx *ctx, uint64_t ticket);
+
 /* Counters: requests finished, site updates performed, windows run, bytes
  * currently held, kernel variant in use.  Any pointer may be NULL. */
 int pkr_ctx_info(pkr_ctx *ctx, int64_t *finished, double *site_updates, int64_t *windows,
@@ -355,7 +363,7 @@ int pkr_ctx_info(pkr_ctx *ctx, int64_t *finished, double *site_updates, int64_t 
 
 /* Stop the worker (if any), drop queued and running requests (their phi is
  * not written), free everything.  The context and its tickets are invalid
- * afterwards. */
+ * afterwards.  No other thread may be inside a call on this context. */
 int pkr_ctx_destroy(pkr_ctx *ctx);
 
 /* ---------------------------------------------------------------------

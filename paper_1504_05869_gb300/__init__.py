@@ -201,7 +201,8 @@ class Context:
 
     def submit(self, rho, phi, shape=None, **kw):
         """Queue a solve; rho/phi device tensors or host arrays (kept alive
-        here until the request finishes).  kw: problem() arguments."""
+        here until poll or wait sees the request finished).  kw: problem()
+        arguments."""
         prob = problem(self.lattice, shape if shape is not None else rho.shape, self.order,
                        precision=self.precision, **kw)
         rp, rh = _ptr(rho)
@@ -217,12 +218,24 @@ class Context:
     def poll(self, ticket):
         st = pkr_stats()
         rc = _pkr.pkr_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(st))
+        if rc != PKR_EBUSY:
+            self._keep.pop(ticket, None)   # the library no longer touches rho/phi
         return rc, (st.as_dict() if rc != PKR_EBUSY else None)
 
     def wait(self, ticket):
         st = pkr_stats()
         rc = _pkr.pkr_ctx_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(st))
+        if rc != PKR_EBUSY:
+            self._keep.pop(ticket, None)
         return rc, st.as_dict()
+
+    def release(self, ticket):
+        """Forget a finished request (pkr_ctx_release): its ticket becomes
+        invalid.  Returns PKR_OK, PKR_EBUSY (not finished) or PKR_EINVAL."""
+        rc = _pkr.pkr_ctx_release(self._h, ctypes.c_uint64(ticket))
+        if rc == 0:
+            self._keep.pop(ticket, None)
+        return rc
 
     def run(self, max_windows=0):
         check(_pkr.pkr_ctx_run(self._h, int(max_windows)), "pkr_ctx_run")

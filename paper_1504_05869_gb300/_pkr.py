@@ -33,7 +33,7 @@ EXPORTS = [
     "pkr_plan_populations", "pkr_solve", "pkr_residual_noalloc", "pkr_variant_count",
     "pkr_plan_autotune", "pkr_ctx_create", "pkr_submit", "pkr_poll", "pkr_ctx_run",
     "pkr_ctx_wait", "pkr_ctx_info", "pkr_ctx_destroy", "pkr_plan_import",
-    "pkr_fixed_point_fft",
+    "pkr_fixed_point_fft", "pkr_ctx_release",
 ]
 
 
@@ -103,6 +103,7 @@ _SIGS = {
     "pkr_ctx_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(pkr_stats)]),
     "pkr_ctx_info": (ctypes.c_int, [_P, _I64, _D, _I64, ctypes.POINTER(ctypes.c_size_t), _I32]),
     "pkr_ctx_destroy": (ctypes.c_int, [_P]),
+    "pkr_ctx_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "pkr_plan_import": (ctypes.c_int, [_P, _P]),
 }
 
@@ -171,4 +172,5 @@ pkr_ctx_run = _fn("pkr_ctx_run")
 pkr_ctx_wait = _fn("pkr_ctx_wait")
 pkr_ctx_info = _fn("pkr_ctx_info")
 pkr_ctx_destroy = _fn("pkr_ctx_destroy")
+pkr_ctx_release = _fn("pkr_ctx_release")
 pkr_plan_import = _fn("pkr_plan_import")

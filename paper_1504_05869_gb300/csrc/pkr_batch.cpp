@@ -121,6 +121,7 @@ struct Job {
     double prev_res = INFINITY;          // residual at the previous check (binary32 lane)
     double t_submit = 0;
     int small = 0;
+    int waiters = 0;                     // threads blocked in pkr_ctx_wait on this ticket
 };
 
 // One batch of grids stored in one precision, advanced by one persistent
@@ -868,10 +869,25 @@ int pkr_ctx_wait(pkr_ctx* C, uint64_t ticket, pkr_stats* st)
             if (r == 0 && j->status == PKR_EBUSY) return PKR_EINVAL;
         }
     } else {
+        j->waiters += 1;
         C->cv_done.wait(lk, [&] { return j->status != PKR_EBUSY || C->stop; });
+        j->waiters -= 1;
     }
     if (st && j->status != PKR_EBUSY) *st = j->st;
     return j->status;
+}
+int pkr_ctx_release(pkr_ctx* C, uint64_t ticket)
+{
+    if (!C) return PKR_EINVAL;
+    std::lock_guard<std::mutex> lk(C->mu);
+    auto it = C->jobs.find(ticket);
+    if (it == C->jobs.end()) return PKR_EINVAL;
+    Job* j = it->second;
+    // a finished request holds no device memory and sits in no queue or lane
+    if (j->status == PKR_EBUSY || j->waiters > 0) return PKR_EBUSY;
+    C->jobs.erase(it);
+    delete j;
+    return PKR_OK;
 }
 
 int pkr_ctx_run(pkr_ctx* C, int64_t max_windows)

@@ -235,4 +235,5 @@ def test_null_handles_and_pointers_rejected(pkr):
     assert L.pkr_ctx_wait(None, 0, ctypes.byref(st)) == -1
     assert L.pkr_ctx_run(None, 1) == -1
     assert L.pkr_ctx_info(None, None, None, None, None, None) == -1
+    assert L.pkr_ctx_release(None, 1) == -1
     assert L.pkr_ctx_destroy(None) == 0

@@ -221,3 +221,28 @@ def test_fp32_batch_mass_drift_is_removed(pk):
     got = phi.cpu().numpy()
     assert abs(got.mean()) < 1e-7 * np.sqrt((got ** 2).mean())
     assert _rel(got, star) < 2e-6
+
+
+def test_release_forgets_finished_requests(pk):
+    """pkr_ctx_release frees the record of a finished request and refuses a
+    queued one; a released ticket is unknown afterwards.  The binding drops
+    its references to rho and phi once poll sees a final status."""
+    import torch
+    ctx = pk.Context("D3Q111", 5, precision="fp64", check_every=8, hbm_budget_bytes=10 ** 9)
+    rho, _ = stiff_source((8, 8, 8), count=2, sigma=1.5, seed=21)
+    r = torch.from_numpy(rho).cuda()
+    phi = torch.zeros_like(r)
+    t = ctx.submit(r, phi, tau_lb=1.3, tol=1e-8, tol_kind="rel_l2", max_sweeps=20000)
+    assert ctx.release(t) == pk.PKR_EBUSY        # queued, not finished
+    assert t in ctx._keep
+    ctx.run()
+    rc, st = ctx.poll(t)
+    assert rc == 0 and st["residual"] < 1e-8
+    assert t not in ctx._keep
+    ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.3, max_steps=st["sweeps"]).phi
+    assert _rel(phi.cpu().numpy(), ref) <= 1e-12
+    assert ctx.release(t) == 0
+    assert ctx.poll(t)[0] == -1                   # unknown ticket now
+    assert ctx.release(t) == -1
+    assert ctx.info()["finished"] == 1
+    ctx.close()
