@@ -166,9 +166,17 @@ int pkr_lattice_info(int lattice, int order, int32_t *Q, int32_t *dim, int32_t *
  * diffusion equation").  Host only. */
 int pkr_tau_from_knudsen(int lattice, double knudsen, const int64_t n[3], double *tau_lb);
 
-/* Number of compiled sweep-kernel geometries for a lattice (velocity groups
- * per 32-site tile x tiles per block).  Host only; < 0 for an unknown lattice. */
+/* Number of compiled sweep-kernel geometries of a plan for a lattice: the
+ * staged ones (velocity groups per 32-site tile x tiles per block) first,
+ * then, for sets of more than 64 velocities, the warp-specialised one (loader
+ * warps filling a ring of tile slots, groups of compute warps draining it).
+ * Host only; < 0 for an unknown lattice. */
 int pkr_variant_count(int lattice);
+
+/* Number of compiled geometries of the batch sweep (pkr_ctx_config.variant
+ * ranges over 0 .. count - 1): the staged ones only.  Host only; < 0 for an
+ * unknown lattice. */
+int pkr_batch_variant_count(int lattice);
 
 /* Device bytes a plan for this problem allocates (populations, source, Phi,
  * scratch).  Host only. */
@@ -312,8 +320,9 @@ typedef struct pkr_ctx_config {
                                  PKR_MIXED_FX64, for every request */
     int32_t check_every;      /* K: steps per graph replay and per residual check (>= 1) */
     size_t hbm_budget_bytes;  /* device bytes the live requests may hold */
-    int32_t variant;          /* >= 0: kernel geometry; -1: library default;
-                                 -2: autotune on a probe grid of edge probe_edge */
+    int32_t variant;          /* 0 .. pkr_batch_variant_count - 1: kernel geometry;
+                                 -1: library default; -2: autotune on a probe grid
+                                 of edge probe_edge */
     int32_t probe_edge;       /* edge of the cubic probe grid for variant = -2 */
     int32_t threaded;         /* 1: a worker thread drives the batch; 0: pkr_ctx_run does */
     int32_t max_grids;        /* most requests live at once (<= 0: 4096) */

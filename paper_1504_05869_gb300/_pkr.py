@@ -31,6 +31,7 @@ EXPORTS = [
     "pkr_plan_bytes", "pkr_plan_create", "pkr_plan_destroy", "pkr_plan_load_source",
     "pkr_plan_run", "pkr_plan_sweeps", "pkr_plan_phi", "pkr_plan_steps",
     "pkr_plan_populations", "pkr_solve", "pkr_residual_noalloc", "pkr_variant_count",
+    "pkr_batch_variant_count",
     "pkr_plan_autotune", "pkr_ctx_create", "pkr_submit", "pkr_poll", "pkr_ctx_run",
     "pkr_ctx_wait", "pkr_ctx_info", "pkr_ctx_destroy", "pkr_plan_import",
     "pkr_fixed_point_fft", "pkr_ctx_release",
@@ -94,6 +95,7 @@ _SIGS = {
     "pkr_fixed_point_fft": (ctypes.c_int, [ctypes.POINTER(pkr_problem), _P, _P, ctypes.c_int,
                                            ctypes.POINTER(pkr_stats), _P]),
     "pkr_variant_count": (ctypes.c_int, [ctypes.c_int]),
+    "pkr_batch_variant_count": (ctypes.c_int, [ctypes.c_int]),
     "pkr_plan_autotune": (ctypes.c_int, [_P, ctypes.c_int, _I32, _D]),
     "pkr_ctx_create": (ctypes.c_int, [ctypes.POINTER(pkr_ctx_config), _P, ctypes.POINTER(_P)]),
     "pkr_submit": (ctypes.c_int, [_P, ctypes.POINTER(pkr_problem), _P, _P, ctypes.c_int,
@@ -164,6 +166,7 @@ pkr_solve = _fn("pkr_solve")
 pkr_residual_noalloc = _fn("pkr_residual_noalloc")
 pkr_fixed_point_fft = _fn("pkr_fixed_point_fft")
 pkr_variant_count = _fn("pkr_variant_count")
+pkr_batch_variant_count = _fn("pkr_batch_variant_count")
 pkr_plan_autotune = _fn("pkr_plan_autotune")
 pkr_ctx_create = _fn("pkr_ctx_create")
 pkr_submit = _fn("pkr_submit")

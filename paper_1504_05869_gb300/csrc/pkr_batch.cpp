@@ -34,9 +34,26 @@
 namespace pkr {
 template <class L, typename T> int launch_batch_t(int, BatchState*, int, int, void*);
 template <class L, typename T> int batch_occupancy_t(int, int*);
-template <class L> int variant_count_t();
+template <class L> int batch_variant_count_t();
 
 namespace {
+
+// Compiled geometries of the batch sweep (the staged ones; the plan sweep's
+// warp-specialised variants have no batch form).
+int batch_variant_count(int lattice)
+{
+    switch (lattice) {
+    case PKR_D1Q5: return batch_variant_count_t<D1Q5>();
+    case PKR_D1Q9: return batch_variant_count_t<D1Q9>();
+    case PKR_D1Q13: return batch_variant_count_t<D1Q13>();
+    case PKR_D2Q25: return batch_variant_count_t<D2Q25>();
+    case PKR_D2Q81: return batch_variant_count_t<D2Q81>();
+    case PKR_D2Q169: return batch_variant_count_t<D2Q169>();
+    case PKR_D3Q19: return batch_variant_count_t<D3Q19>();
+    case PKR_D3Q111: return batch_variant_count_t<D3Q111>();
+    }
+    return -1;
+}
 
 template <class L>
 int batch_launch_l(int prec, int var, BatchState* st, int K, int grid, void* s)
@@ -743,7 +760,7 @@ int pkr_ctx_create(const pkr_ctx_config* cfg, void* stream, pkr_ctx** out)
     LatticeInfo li;
     int rc = build_lattice(cfg->lattice, cfg->order, &li);
     if (rc != PKR_OK) return rc;
-    const int nvar = pkr_variant_count(cfg->lattice);
+    const int nvar = batch_variant_count(cfg->lattice);
     if (cfg->variant >= nvar || cfg->variant < -2) return PKR_EINVAL;
     pkr_ctx* C = new (std::nothrow) pkr_ctx();
     if (!C) return PKR_ENOMEM;
@@ -795,6 +812,8 @@ int pkr_ctx_create(const pkr_ctx_config* cfg, void* stream, pkr_ctx** out)
     *out = C;
     return PKR_OK;
 }
+
+int pkr_batch_variant_count(int lattice) { return batch_variant_count(lattice); }
 
 int pkr_submit(pkr_ctx* C, const pkr_problem* p, const double* rho, double* phi, int host_buffers,
                uint64_t* ticket)
@@ -960,7 +979,7 @@ namespace {
 // every request of the context sees the same kernels.
 int tune_variant(pkr_ctx* C, Lane& L, int edge)
 {
-    const int nvar = pkr_variant_count(C->cfg.lattice);
+    const int nvar = batch_variant_count(C->cfg.lattice);
     Job probe;
     probe.prob.n[0] = edge;
     probe.prob.n[1] = C->li.dim >= 2 ? edge : 1;

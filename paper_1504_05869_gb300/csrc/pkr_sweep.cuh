@@ -344,6 +344,156 @@ __device__ __forceinline__ double pow2(int e)
     return __longlong_as_double((long long)(1023 + e) << 52);
 }
 
+// The part of a tile step that follows the pull, for velocity group g of G
+// (velocities lo(g) .. lo(g + 1) - 1): the group's share of the density
+// (the G warps of a tile meet at named barrier `bar`, twice in binary64 and
+// once otherwise; every meeting sits outside lane-dependent branches), the
+// relaxation and store of the group's velocities, and, in group 0, the
+// density output and the residual terms.  sbase: this lane's column of the
+// group's staged values (velocity lo(g) first, 32 values per velocity);
+// xacc, xexp: the tile's exchange rows.
+template <class L, typename T, int G, int g>
+__device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
+                                              const Coefs<typename AccType<T>::type>& c,
+                                              int mode, bool valid, int s,
+                                              typename AccType<T>::type Sx, int lane,
+                                              uint32_t sbase, int bar, long long (&xacc)[G][32],
+                                              int (&xexp)[G][32], double& d2, double& n2,
+                                              double& mx, double& ms, unsigned long long& fxm)
+{
+    using R = typename AccType<T>::type;
+    constexpr int lo = g * L::Q / G;
+    constexpr int hi = (g + 1) * L::Q / G;
+    constexpr int n = hi - lo;
+    constexpr int NC = ncls_of<L>();
+    constexpr int GB = 63 - 53 - ceil_log2(L::Q);
+    T* __restrict__ B = tg.B;
+    const int64_t V = tg.V;
+    R Phi;
+    if constexpr (std::is_same<T, long long>::value) {
+        // fixed point: the density is an exact integer sum
+        long long part = 0;
+#pragma unroll 8
+        for (int k = 0; k < n; ++k) part += lds_s64(sbase + k * 256);
+        if constexpr (G > 1) {
+            xacc[g][lane] = part;
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
+            part = 0;
+#pragma unroll
+            for (int k = 0; k < G; ++k) part += xacc[k][lane];
+        }
+        Phi = (double)part * pow2(-tg.fr);
+    } else if constexpr (std::is_same<T, double>::value) {
+        int emax = max_exponent<n>(sbase);
+        if constexpr (G > 1) {
+            xexp[g][lane] = emax;
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
+#pragma unroll
+            for (int k = 0; k < G; ++k) emax = max(emax, xexp[k][lane]);
+        }
+        const bool plain = plain_path(emax);
+        long long part = plain ? __double_as_longlong(plain_sum<n>(sbase))
+                               : fixed_sum<GB, n>(sbase, emax);
+        if constexpr (G > 1) {
+            xacc[g][lane] = part;
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
+            if (plain) {
+                double t = 0.0;
+#pragma unroll
+                for (int k = 0; k < G; ++k) t += __longlong_as_double(xacc[k][lane]);
+                Phi = t;
+            } else {
+                long long t = 0;
+#pragma unroll
+                for (int k = 0; k < G; ++k) t += xacc[k][lane];
+                Phi = fixed_value<GB>(t, emax);
+            }
+        } else {
+            Phi = plain ? __longlong_as_double(part) : fixed_value<GB>(part, emax);
+        }
+    } else {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 2
+        for (int k = 0; k + 3 < n; k += 4) {
+            s0 += lds_f32(sbase + (k + 0) * 128);
+            s1 += lds_f32(sbase + (k + 1) * 128);
+            s2 += lds_f32(sbase + (k + 2) * 128);
+            s3 += lds_f32(sbase + (k + 3) * 128);
+        }
+#pragma unroll
+        for (int k = n - n % 4; k < n; ++k) s0 += lds_f32(sbase + k * 128);
+        float part = (s0 + s1) + (s2 + s3);
+        if constexpr (G > 1) {
+            // binary32 partials meet in group order (fixed, deterministic)
+            xacc[g][lane] = (long long)__float_as_int(part);
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
+            part = 0.f;
+#pragma unroll
+            for (int k = 0; k < G; ++k) part += __int_as_float((int)xacc[k][lane]);
+        }
+        Phi = part;
+    }
+
+    // relax and store this group's velocities, one symmetry class at a
+    // time (velocities of a class are contiguous and share phi_c, chi_c)
+    if (valid) {
+        static_for<0, NC>([&](auto CI) {
+            constexpr int cl = decltype(CI)::value;
+            constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
+            constexpr int i0 = cb > lo ? cb : lo;
+            constexpr int i1 = ce < hi ? ce : hi;
+            if constexpr (i0 < i1 && std::is_same<T, long long>::value) {
+                const double e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
+                const long long ei = __double2ll_rn(e * pow2(tg.fw));
+                // the written array's scale is 2^-k that of the read one (k >= 0,
+                // the rescale only lowers it): fold 2^-k into the coefficient
+                const int k = tg.fr - tg.fw;
+                const long long cw = k == 0 ? tg.cfx : ((tg.cfx >> (k - 1)) + 1) >> 1;
+                T* dst = B + ((int64_t)i0 * V + s);
+#pragma unroll 4
+                for (int i = i0; i < i1; ++i) {
+                    const long long p = fx_mul(lds_s64(sbase + (i - lo) * 256), cw) + ei;
+                    fxm |= (unsigned long long)(p ^ (p >> 63));
+                    store_stream(dst, (T)p);
+                    dst += V;
+                }
+            } else if constexpr (i0 < i1) {
+                const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
+                T* dst = B + ((int64_t)i0 * V + s);
+                int i = i0;
+                for (; i + 3 < i1; i += 4) {
+                    const R g0 = lds_val<T>(sbase + (i + 0 - lo) * 32 * sizeof(T));
+                    const R g1 = lds_val<T>(sbase + (i + 1 - lo) * 32 * sizeof(T));
+                    const R g2 = lds_val<T>(sbase + (i + 2 - lo) * 32 * sizeof(T));
+                    const R g3 = lds_val<T>(sbase + (i + 3 - lo) * 32 * sizeof(T));
+                    store_stream(dst, (T)fma(c.om1, g0, e));
+                    store_stream(dst + V, (T)fma(c.om1, g1, e));
+                    store_stream(dst + 2 * V, (T)fma(c.om1, g2, e));
+                    store_stream(dst + 3 * V, (T)fma(c.om1, g3, e));
+                    dst += 4 * V;
+                }
+                for (; i < i1; ++i) {
+                    const R gi = lds_val<T>(sbase + (i - lo) * 32 * sizeof(T));
+                    store_stream(dst, (T)fma(c.om1, gi, e));
+                    dst += V;
+                }
+            }
+        });
+    }
+    // density output and residual contributions (one group per tile)
+    if (g == 0 && mode != kPlain && valid) {
+        const double ph = (double)Phi;
+        if (mode == kCheck) {
+            const double d = ph - tg.Phi[s];
+            d2 += d * d;
+            n2 += ph * ph;
+            mx = fmax(mx, fabs(d));
+            ms += ph;
+        }
+        tg.Phi[s] = ph;
+    }
+}
+
 // One 32-site tile of one grid, executed by the G warps of a tile slot:
 // pull (cp.async), density, relax + store, density output.  On check sweeps
 // the lane's contributions to |dPhi|^2, |Phi|^2, max |dPhi| and sum Phi are
@@ -360,11 +510,8 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
     using ST = Staged<L, T, G, TILES>;
     constexpr int RC = reach_of<L>();
     constexpr int W = 2 * RC + 1;
-    constexpr int NC = ncls_of<L>();
-    constexpr int GB = 63 - 53 - ceil_log2(L::Q);
-    static_assert(GB >= 1, "too many velocities for the 64-bit density sum");
+    static_assert(63 - 53 - ceil_log2(L::Q) >= 1, "too many velocities for the 64-bit density sum");
     const T* __restrict__ A = tg.A;
-    T* __restrict__ B = tg.B;
     const int64_t V = tg.V;
     const int nx = tg.nx, ny = tg.ny, nz = tg.nz;
     const int nxy = nx * ny;
@@ -404,7 +551,6 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
         constexpr int g = decltype(GI)::value;
         constexpr int lo = ST::lo(g);
         constexpr int hi = ST::lo(g + 1);
-        constexpr int n = hi - lo;
         if (grp != g) return;
         // pull: one asynchronous copy per velocity of this group
         static_for<lo, hi>([&](auto I) {
@@ -417,131 +563,8 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
         });
         cp_async_wait_all();
 
-        // density (the G warps of a tile meet twice at named barrier 1 + sub;
-        // both barriers sit outside every lane-dependent branch)
-        R Phi;
-        if constexpr (std::is_same<T, long long>::value) {
-            // fixed point: the density is an exact integer sum
-            long long part = 0;
-#pragma unroll 8
-            for (int k = 0; k < n; ++k) part += lds_s64(sbase + k * 256);
-            if constexpr (G > 1) {
-                xacc[sub][g][lane] = part;
-                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
-                part = 0;
-#pragma unroll
-                for (int k = 0; k < G; ++k) part += xacc[sub][k][lane];
-            }
-            Phi = (double)part * pow2(-tg.fr);
-        } else if constexpr (std::is_same<T, double>::value) {
-            int emax = max_exponent<n>(sbase);
-            if constexpr (G > 1) {
-                xexp[sub][g][lane] = emax;
-                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
-#pragma unroll
-                for (int k = 0; k < G; ++k) emax = max(emax, xexp[sub][k][lane]);
-            }
-            const bool plain = plain_path(emax);
-            long long part = plain ? __double_as_longlong(plain_sum<n>(sbase))
-                                   : fixed_sum<GB, n>(sbase, emax);
-            if constexpr (G > 1) {
-                xacc[sub][g][lane] = part;
-                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
-                if (plain) {
-                    double t = 0.0;
-#pragma unroll
-                    for (int k = 0; k < G; ++k) t += __longlong_as_double(xacc[sub][k][lane]);
-                    Phi = t;
-                } else {
-                    long long t = 0;
-#pragma unroll
-                    for (int k = 0; k < G; ++k) t += xacc[sub][k][lane];
-                    Phi = fixed_value<GB>(t, emax);
-                }
-            } else {
-                Phi = plain ? __longlong_as_double(part) : fixed_value<GB>(part, emax);
-            }
-        } else {
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll 2
-            for (int k = 0; k + 3 < n; k += 4) {
-                s0 += lds_f32(sbase + (k + 0) * 128);
-                s1 += lds_f32(sbase + (k + 1) * 128);
-                s2 += lds_f32(sbase + (k + 2) * 128);
-                s3 += lds_f32(sbase + (k + 3) * 128);
-            }
-#pragma unroll
-            for (int k = n - n % 4; k < n; ++k) s0 += lds_f32(sbase + k * 128);
-            float part = (s0 + s1) + (s2 + s3);
-            if constexpr (G > 1) {
-                // binary32 partials meet in group order (fixed, deterministic)
-                xacc[sub][g][lane] = (long long)__float_as_int(part);
-                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
-                part = 0.f;
-#pragma unroll
-                for (int k = 0; k < G; ++k) part += __int_as_float((int)xacc[sub][k][lane]);
-            }
-            Phi = part;
-        }
-
-        // relax and store this group's velocities, one symmetry class at a
-        // time (velocities of a class are contiguous and share phi_c, chi_c)
-        if (valid) {
-            static_for<0, NC>([&](auto CI) {
-                constexpr int cl = decltype(CI)::value;
-                constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
-                constexpr int i0 = cb > lo ? cb : lo;
-                constexpr int i1 = ce < hi ? ce : hi;
-                if constexpr (i0 < i1 && std::is_same<T, long long>::value) {
-                    const double e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
-                    const long long ei = __double2ll_rn(e * pow2(tg.fw));
-                    // the written array's scale is 2^-k that of the read one (k >= 0,
-                    // the rescale only lowers it): fold 2^-k into the coefficient
-                    const int k = tg.fr - tg.fw;
-                    const long long cw = k == 0 ? tg.cfx : ((tg.cfx >> (k - 1)) + 1) >> 1;
-                    T* dst = B + ((int64_t)i0 * V + s);
-#pragma unroll 4
-                    for (int i = i0; i < i1; ++i) {
-                        const long long p = fx_mul(lds_s64(sbase + (i - lo) * 256), cw) + ei;
-                        fxm |= (unsigned long long)(p ^ (p >> 63));
-                        store_stream(dst, (T)p);
-                        dst += V;
-                    }
-                } else if constexpr (i0 < i1) {
-                    const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
-                    T* dst = B + ((int64_t)i0 * V + s);
-                    int i = i0;
-                    for (; i + 3 < i1; i += 4) {
-                        const R g0 = lds_val<T>(sbase + (i + 0 - lo) * 32 * sizeof(T));
-                        const R g1 = lds_val<T>(sbase + (i + 1 - lo) * 32 * sizeof(T));
-                        const R g2 = lds_val<T>(sbase + (i + 2 - lo) * 32 * sizeof(T));
-                        const R g3 = lds_val<T>(sbase + (i + 3 - lo) * 32 * sizeof(T));
-                        store_stream(dst, (T)fma(c.om1, g0, e));
-                        store_stream(dst + V, (T)fma(c.om1, g1, e));
-                        store_stream(dst + 2 * V, (T)fma(c.om1, g2, e));
-                        store_stream(dst + 3 * V, (T)fma(c.om1, g3, e));
-                        dst += 4 * V;
-                    }
-                    for (; i < i1; ++i) {
-                        const R gi = lds_val<T>(sbase + (i - lo) * 32 * sizeof(T));
-                        store_stream(dst, (T)fma(c.om1, gi, e));
-                        dst += V;
-                    }
-                }
-            });
-        }
-        // density output and residual contributions (one group per tile)
-        if (g == 0 && mode != kPlain && valid) {
-            const double ph = (double)Phi;
-            if (mode == kCheck) {
-                const double d = ph - tg.Phi[s];
-                d2 += d * d;
-                n2 += ph * ph;
-                mx = fmax(mx, fabs(d));
-                ms += ph;
-            }
-            tg.Phi[s] = ph;
-        }
+        group_compute<L, T, G, g>(tg, c, mode, valid, s, Sx, lane, sbase, 1 + sub, xacc[sub],
+                                  xexp[sub], d2, n2, mx, ms, fxm);
     });
     __syncwarp();
 }
@@ -1046,6 +1069,12 @@ int launch_stencil(const double* Pin, double* Pout, const double* St, const Coef
     return (int)cudaGetLastError();
 }
 
+}  // namespace pkr
+
+#include "pkr_sweep_ws.cuh"
+
+namespace pkr {
+
 template <class L, typename T, int K>
 int launch_variant(const SweepArgs& a, const void* coefs, int grid, void* stream)
 {
@@ -1072,7 +1101,8 @@ int occupancy_variant(int* blocks, int* tiles_per_block)
                                                               ST::smem_bytes());
 }
 
-// Run-time dispatch over the compiled variants of (L, T).
+// Run-time dispatch over the compiled variants of (L, T): the staged
+// geometries of Variants<L>, then the warp-specialised ones of WsVariants<L>.
 template <class L, typename T>
 int launch_sweep_t(int variant, const SweepArgs& a, const void* coefs, int grid, void* stream)
 {
@@ -1080,6 +1110,10 @@ int launch_sweep_t(int variant, const SweepArgs& a, const void* coefs, int grid,
     static_for<0, Variants<L>::N>([&](auto K) {
         if (variant == decltype(K)::value)
             rc = launch_variant<L, T, decltype(K)::value>(a, coefs, grid, stream);
+    });
+    static_for<0, WsVariants<L>::N>([&](auto K) {
+        if (variant == Variants<L>::N + decltype(K)::value)
+            rc = launch_ws_variant<L, T, decltype(K)::value>(a, coefs, grid, stream);
     });
     return rc;
 }
@@ -1092,11 +1126,19 @@ int occupancy_t(int variant, int* blocks, int* tiles_per_block)
         if (variant == decltype(K)::value)
             rc = occupancy_variant<L, T, decltype(K)::value>(blocks, tiles_per_block);
     });
+    static_for<0, WsVariants<L>::N>([&](auto K) {
+        if (variant == Variants<L>::N + decltype(K)::value)
+            rc = occupancy_ws_variant<L, T, decltype(K)::value>(blocks, tiles_per_block);
+    });
     return rc;
 }
 
+// Variants of a plan's sweep (staged, then warp-specialised) and of the
+// batch sweep (staged only).
 template <class L>
-int variant_count_t() { return Variants<L>::N; }
+int variant_count_t() { return Variants<L>::N + WsVariants<L>::N; }
+template <class L>
+int batch_variant_count_t() { return Variants<L>::N; }
 
 #define PKR_INSTANTIATE_SWEEP(L)                                                             \
     template int launch_sweep_t<L, double>(int, const SweepArgs&, const void*, int, void*); \
@@ -1106,6 +1148,7 @@ int variant_count_t() { return Variants<L>::N; }
     template int occupancy_t<L, double>(int, int*, int*);                                    \
     template int occupancy_t<L, float>(int, int*, int*);                                     \
     template int variant_count_t<L>();                                                      \
+    template int batch_variant_count_t<L>();                                                \
     template int launch_sweep_h16<L>(const SweepArgs&, const void*, int, void*);             \
     template int occupancy_h16<L>(int*, int*);                                               \
     template int launch_stencil<L>(const double*, double*, const double*, const Coefs<double>&,  \

@@ -173,6 +173,14 @@ def test_context_config_validation(pk_cfg=None):
     assert create(precision=3) == -1      # binary16 storage: pkr_solve only
     assert create(precision=8) == -1
     assert create(variant=99) == -1
+    # the plan sweep's warp-specialised variants have no batch form
+    nb = pk._pkr.pkr_batch_variant_count(pk.LATTICES["D3Q111"])
+    assert 0 < nb < pk._pkr.pkr_variant_count(pk.LATTICES["D3Q111"])
+    assert create(variant=nb) == -1
+    for name in ("D1Q5", "D3Q19"):
+        assert pk._pkr.pkr_batch_variant_count(pk.LATTICES[name]) == \
+            pk._pkr.pkr_variant_count(pk.LATTICES[name])
+    assert pk._pkr.pkr_batch_variant_count(42) < 0
     assert create(order=7) == -1
     assert create(lattice=42) == -1
 

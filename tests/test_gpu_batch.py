@@ -123,7 +123,7 @@ def test_autotuned_context_and_errors(pk):
     import torch
     ctx = pk.Context("D3Q111", 5, precision="fp32", check_every=4, variant=-2, probe_edge=24,
                      hbm_budget_bytes=10 ** 9)
-    assert 0 <= ctx.info()["variant"] < pk._pkr.pkr_variant_count(pk.LATTICES["D3Q111"])
+    assert 0 <= ctx.info()["variant"] < pk._pkr.pkr_batch_variant_count(pk.LATTICES["D3Q111"])
     big = torch.zeros((128, 128, 128), dtype=torch.float64, device="cuda")
     with pytest.raises(pk.PkrError) as e:     # alone exceeds the budget
         ctx.submit(big, big.clone(), tau_lb=1.3, tol=1e-6)
@@ -245,4 +245,64 @@ def test_release_forgets_finished_requests(pk):
     assert ctx.poll(t)[0] == -1                   # unknown ticket now
     assert ctx.release(t) == -1
     assert ctx.info()["finished"] == 1
+    ctx.close()
+
+
+def _impulse_response(tau, steps):
+    lat = oracle.lattice("D3Q111", 5)
+    R = lat.reach * steps
+    m = 2 * R + 1
+    S = np.zeros((m, m, m))
+    S[R, R, R] = 1.0
+    return oracle.solve(S, "D3Q111", 5, tau_lb=tau, max_steps=steps, S=S).phi, R
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,bar", [("fp32", 2e-5), ("fp64", 1e-13), ("fx64", 1e-12)])
+def test_batch_at_workload_sizes_sampled(pk, precision, bar):
+    """The batch kernel at the batching workload's grid sizes: the first 12
+    grids of the seed-2 draw (edges 32-128, 1-16 Gaussians, Kn 0.2 each, 85k to
+    626k sites, hundreds to thousands of tiles per grid) plus two tiny grids
+    (one with edges shorter than the lattice reach), in one context with
+    K = 4, run for two windows (7 steps, tol 0).  For every grid, Phi at 28
+    sampled sites equals the oracle's 7-step impulse response at that grid's
+    tau convolved with that grid's source, evaluated one site at a time;
+    bounds are relative to max |Phi| of the grid."""
+    import torch
+    from paper_1504_05869_gb300.workloads import batch_jobs
+    lat = oracle.lattice("D3Q111", 5)
+    grids = [(j.shape, j.rho()) for j in batch_jobs(count=12)]
+    for shape, seed in (((2, 3, 5), 41), ((9, 7, 13), 42)):
+        grids.append((shape, stiff_source(shape, count=3, sigma=1.5, seed=seed)[0]))
+    ctx = pk.Context("D3Q111", 5, precision=precision, check_every=4,
+                     hbm_budget_bytes=40 * 10 ** 9)
+    subs = []
+    for shape, rho in grids:
+        tau = oracle.tau_from_knudsen(0.2, shape, lat.cs2)
+        r = torch.from_numpy(rho).cuda()
+        phi = torch.zeros_like(r)
+        t = ctx.submit(r, phi, tau_lb=tau, tol=0.0, max_sweeps=7)
+        subs.append((shape, rho, tau, r, phi, t))
+    ctx.run()
+    kcache = {}
+    rng = np.random.default_rng(77)
+    for shape, rho, tau, r, phi, t in subs:
+        rc, st = ctx.poll(t)
+        assert rc == 0 and st["sweeps"] == 7, (shape, rc, st)
+        got = phi.cpu().numpy()
+        if tau not in kcache:
+            kcache[tau] = _impulse_response(tau, 7)
+        K, R = kcache[tau]
+        S, _ = oracle.source(rho, lat, tau)
+        off = np.arange(-R, R + 1)
+        sites = [tuple(int(rng.integers(0, shape[a])) for a in range(3)) for _ in range(24)]
+        sites += [(0, 0, 0), (shape[0] - 1, shape[1] - 1, shape[2] - 1),
+                  (0, shape[1] - 1, 0), (shape[0] - 1, 0, shape[2] - 1)]
+        scale = np.abs(got).max()
+        for (z, y, x) in sites:
+            window = S[np.ix_((z - off) % shape[0], (y - off) % shape[1], (x - off) % shape[2])]
+            want = float(np.sum(K * window))
+            assert abs(got[z, y, x] - want) <= bar * scale, (shape, (z, y, x), got[z, y, x], want)
+    info = ctx.info()
+    assert info["finished"] == len(grids) and info["bytes_in_use"] == 0
     ctx.close()

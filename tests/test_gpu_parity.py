@@ -195,32 +195,98 @@ def _impulse_response(lattice, order, tau, steps):
     return K, R
 
 
-@pytest.mark.slow
-def test_full_size_256_sampled(pk):
-    """256^3, 64 Gaussians (sigma 2, seed 0), D3Q111 N=5 at Kn 0.2 in the
-    benchmark's launch configuration.  After 4 steps Phi(x) is the oracle's
-    4-step impulse response convolved with S, evaluated one site at a time."""
-    import torch
+@pytest.fixture(scope="module")
+def full_256():
+    """The benchmark's input: 256^3, 64 Gaussians (sigma 2, seed 0), D3Q111
+    N=5 at Kn 0.2, with the oracle's source S and 4-step impulse response."""
     shape = (256, 256, 256)
     rho, _ = stiff_source(shape, count=64, sigma=2.0, seed=0)
     lat = oracle.lattice("D3Q111", 5)
-    tau = oracle.tau_from_knudsen(0.2, (256, 256, 256), lat.cs2)
-    steps = 4
-    got, rc, st = _gpu_solve(pk, rho, "D3Q111", 5, tau, steps=steps)
-    assert rc == 0
+    tau = oracle.tau_from_knudsen(0.2, shape, lat.cs2)
     S, _ = oracle.source(rho, lat, tau)
-    K, R = _impulse_response("D3Q111", 5, tau, steps)
-    rng = np.random.default_rng(12)
-    sites = [tuple(rng.integers(0, 256, 3)) for _ in range(300)]
-    sites += [(0, 0, 0), (255, 255, 255), (0, 255, 128), (255, 0, 1)]
+    K, R = _impulse_response("D3Q111", 5, tau, 4)
+    return rho, tau, S, K, R
+
+
+def _sampled_diffs(got, S, K, R, seed=12, count=300):
+    """got - (K * S)(x) at sampled sites x, Phi(x) = sum_d K(d) S(x - d)."""
+    n = got.shape
+    rng = np.random.default_rng(seed)
+    sites = [tuple(int(rng.integers(0, n[a])) for a in range(3)) for _ in range(count)]
+    sites += [(0, 0, 0), (n[0] - 1, n[1] - 1, n[2] - 1), (0, n[1] - 1, n[2] // 2),
+              (n[0] - 1, 0, 1)]
     off = np.arange(-R, R + 1)
-    scale = np.abs(got).max()
-    diffs = []
+    out = []
     for (z, y, x) in sites:
-        # Phi(x) = sum_d K(d) S(x - d), K indexed from -R..R
-        window = S[np.ix_((z - off) % 256, (y - off) % 256, (x - off) % 256)]
-        diffs.append(got[z, y, x] - float(np.sum(K * window)))
-    assert np.max(np.abs(diffs)) <= 1e-13 * scale
+        window = S[np.ix_((z - off) % n[0], (y - off) % n[1], (x - off) % n[2])]
+        out.append(got[z, y, x] - float(np.sum(K * window)))
+    return np.abs(np.array(out))
+
+
+# (storage, variant, bound relative to max |Phi|): binary64 and fixed point
+# to 1e-13 / 1e-12 (a few ulps per step of values resolved to 2^-51 of the
+# largest), binary32 to 2e-5 (its parity bound).  Variant -1 is the default
+# launch configuration of the benchmark; 6 is the warp-specialised
+# sweep (3 groups of 4 compute warps, 2 slots each).
+FULL_CASES = [("fp64", -1, 1e-13), ("fp64", 6, 1e-13),
+              ("fx64", -1, 1e-12), ("fx64", 6, 1e-12), ("fp32", -1, 2e-5), ("fp32", 6, 2e-5)]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,variant,bar", FULL_CASES)
+def test_full_size_256_sampled(pk, full_256, precision, variant, bar):
+    """At the benchmark's full size and launch configuration, after 4 steps
+    Phi(x) is the oracle's 4-step impulse response convolved with S,
+    evaluated one site at a time (304 sites)."""
+    import torch
+    rho, tau, S, K, R = full_256
+    prob = pk.problem("D3Q111", rho.shape, 5, tau_lb=tau, max_sweeps=4, precision=precision,
+                      variant=variant)
+    r = torch.from_numpy(rho).cuda()
+    phi = torch.empty_like(r)
+    rc, st = pk.solve(r, phi, prob)
+    assert rc == 0 and st["sweeps"] == 4
+    got = phi.cpu().numpy()
+    del r, phi
+    d = _sampled_diffs(got, S, K, R)
+    assert d.max() <= bar * np.abs(got).max(), d.max() / np.abs(got).max()
+
+
+@pytest.mark.parametrize("lattice,order,shape,prec", [
+    ("D3Q111", 5, (29, 37, 41), "fp64"),
+    ("D3Q111", 5, (29, 37, 41), "fx64"),
+    ("D3Q111", 5, (29, 37, 41), "fp32"),
+    ("D2Q169", 7, (287, 301), "fp64"),
+    ("D2Q81", 5, (250, 330), "fx64"),
+])
+def test_every_variant_many_tiles_per_block(pk, lattice, order, shape, prec):
+    """Grids of ~1400-2700 tiles with a ragged tail, so that every persistent
+    block takes several tiles and the warp-specialised ring of tile slots is
+    reused many times.  Residual checks every 2 steps run inside the steps
+    (tol below reach: the run ends at max_sweeps).  Every variant matches the
+    oracle; binary64 and fixed-point variants agree bit for bit, and the
+    residuals they report agree to rounding."""
+    import torch
+    rho = _rand(shape, 31)
+    steps = 6
+    n = pk._pkr.pkr_variant_count(pk.LATTICES[lattice])
+    ref = oracle.solve(rho, lattice, order, tau_lb=1.3, max_steps=steps).phi
+    outs, res = [], []
+    for v in range(n):
+        prob = pk.problem(lattice, rho.shape, order, tau_lb=1.3, max_sweeps=steps, tol=1e-300,
+                          check_every=2, precision=prec, variant=v)
+        r = torch.from_numpy(rho).cuda()
+        phi = torch.empty_like(r)
+        rc, st = pk.solve(r, phi, prob)
+        assert rc == pk._pkr.PKR_ENOCONV and st["sweeps"] == steps, (v, rc)
+        outs.append(phi.cpu().numpy())
+        res.append(st["residual"])
+    for v, o in enumerate(outs):
+        assert _rel(o, ref) <= (2e-5 if prec == "fp32" else FP64_TOL), (v, _rel(o, ref))
+    if prec != "fp32":
+        for v, o in enumerate(outs[1:], 1):
+            assert np.array_equal(o, outs[0]), v
+        assert max(res) - min(res) <= 1e-12 * max(res)
 
 
 @pytest.mark.parametrize("lattice,order,shape,prec", [
