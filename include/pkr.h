@@ -81,6 +81,12 @@ typedef enum pkr_lattice {
  * arithmetic in binary32, source in binary32; accurate to ~1e-4 of Phi.
  * MIXED16 (pkr_solve only): binary16 to PKR_MIXED16_SWITCH_TOL, binary32 to
  * PKR_MIXED_SWITCH_TOL, then binary64 to tol.
+ * In pkr_solve's ladders (and in contexts) a reduced-precision rung also
+ * hands over when its per-step change stops falling from one check to the
+ * next (from the third check on, and below 0.1 for binary16, 1e-3 for
+ * binary32): its rounding floor can lie above the switch tolerance.  (Tests
+ * can set both switch tolerances of pkr_solve with the environment variable
+ * PKR_TEST_SWITCH_TOL.)
  * FX64: populations stored as 64-bit integers v 2^F with a power-of-two scale
  * per array (F lowered on the device whenever the largest stored value
  * passes 2^54).  The density is an exact integer sum and the relaxation a
@@ -350,11 +356,19 @@ int pkr_poll(pkr_ctx *ctx, uint64_t ticket, pkr_stats *stats);
 
 /* Drive a non-threaded context from the caller's thread: admit what fits and
  * run K-step windows until nothing is queued or live, or max_windows windows
- * have run (max_windows <= 0: no limit).  Returns PKR_OK or PKR_ECUDA. */
+ * have run (max_windows <= 0: no limit).  Several threads may call it (and
+ * pkr_ctx_wait) on one context: one at a time runs a round, the others wait
+ * for that round to end.  Returns PKR_OK or PKR_ECUDA; after PKR_ECUDA every
+ * request that was queued or running has finished with PKR_ECUDA and has
+ * given its device memory back.  (Tests can make the n-th round, counted
+ * from 0 per context, report PKR_ECUDA without launching anything by setting
+ * the environment variable PKR_TEST_FAIL_ROUND=n before pkr_ctx_create.) */
 int pkr_ctx_run(pkr_ctx *ctx, int64_t max_windows);
 
-/* Block until a request has finished (threaded contexts) and return as
- * pkr_poll does. */
+/* Block until a request has finished and return as pkr_poll does.  In a
+ * threaded context the worker drives; in a non-threaded one the caller runs
+ * rounds until the request finishes (PKR_EINVAL if nothing is left to run
+ * and it has not). */
 int pkr_ctx_wait(pkr_ctx *ctx, uint64_t ticket, pkr_stats *stats);
 
 /* Forget a finished request: its ticket becomes invalid and the context's
@@ -377,26 +391,33 @@ int pkr_ctx_destroy(pkr_ctx *ctx);
 
 /* ---------------------------------------------------------------------
  * Allocation-free residual (the paper has no counterpart: this is a service
- * for callers that cannot allocate device memory -- code that runs while a
- * CUDA graph is being captured, runtimes whose device memory all belongs to
- * their own pool, loops that must not touch the allocator).
+ * for callers that cannot allocate device memory -- runtimes whose device
+ * memory all belongs to their own pool and that forbid side allocations, and
+ * loops that must not enter the allocator, where cudaMalloc and cudaFree can
+ * synchronise the device).
  *
  * Computes, in binary64 with a fixed reduction order, the same change of Phi
  * that the solver's stopping rule uses:
  *     out[0] = max_x |phi_new - phi_old|
  *     out[1] = ||phi_new - phi_old||_2 / ||phi_new||_2   (0 if both vanish,
- *              +inf if only phi_new does; NaN if an input holds NaN)
+ *              +inf if only phi_new does)
  *     out[2] = ||phi_new||_2
+ * For finite inputs whose squares and sums stay finite these are finite
+ * (out[1] may be +inf as stated).  If an input holds NaN, out[0] and out[1]
+ * are NaN.  If an input holds +-inf, or a square or a sum overflows, the
+ * binary64 arithmetic decides: out[1] can then be NaN (inf / inf) although
+ * no input is NaN, so a NaN in out[1] means "not finite", not "NaN input".
  * phi_new, phi_old: device pointers to V doubles each.  out: host pointer to
  * 3 doubles.  The call queues two kernels on `stream`, copies out[] back and
- * synchronises the stream.
+ * synchronises the stream before it returns.
  *
  * Memory: no cudaMalloc, cudaFree or allocating library routine is called.
- * The scratch (block partials and the three results, 24.6 KB) is a static
- * device array of the library, held on every GPU that loads the library
- * until the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  All calls on a device share the
+ * The scratch (at most 1024 block partials of 3 doubles and the three
+ * results, 24.6 KB) is a static device array of the library, held on every
+ * GPU that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.  All
+ * calls on a device share the
  * array and it keeps the last call's contents, so calls that overlap on the
  * GPU (different streams, no ordering between them) race: order them.
  *

@@ -135,6 +135,10 @@ struct pkr_plan {
     LatticeInfo lat;
     double tau_lb, omega, scale, rho_mean, last_residual, last_res3[3];
     double soff_next;   // source offset for the next launch (mass correction)
+    // > 0: a reduced-precision rung of pkr_solve's ladder, which hands over
+    // (pkr_plan_run returns PKR_OK) once the residual, below this cap, stops
+    // falling from one check to the next (the storage's rounding floor)
+    double stall_cap;
     cudaStream_t stream;
     int device, grid, red_blocks, elem, small, variant, nsm;
     int64_t ntiles;
@@ -857,7 +861,7 @@ int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check
     const int64_t K = check_every > 0 ? check_every : P->prob.check_every;
     const double t0 = now_ms();
     int status = PKR_OK;
-    double min_res = INFINITY;
+    double min_res = INFINITY, prev_res = INFINITY;
     int nchecks = 0;
     int64_t done = 0;
     bool stopped = false;
@@ -933,6 +937,8 @@ int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check
             }
             if (r < min_res) min_res = r;
             if (tol > 0.0 && r < tol) break;
+            if (P->stall_cap > 0.0 && nchecks > 2 && r >= prev_res && r < P->stall_cap) break;
+            prev_res = r;
         }
     }
     PKR_CK(cudaStreamSynchronize(P->stream));
@@ -974,15 +980,22 @@ int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buf
     const double t0 = now_ms();
     // Precision ladder: each stage runs to its switch tolerance (or tol, if
     // looser), then the next, wider stage continues from the converted state.
+    // A reduced-precision rung also hands over when its residual stops
+    // falling below a cap (binary16: 0.1, binary32: 1e-3), as batch contexts
+    // do: its rounding floor may lie above the switch tolerance.  (Tests can
+    // lower both switch tolerances with the environment variable
+    // PKR_TEST_SWITCH_TOL, so that the rungs end at their floor.)
+    double sw16 = PKR_MIXED16_SWITCH_TOL, sw32 = PKR_MIXED_SWITCH_TOL;
+    if (const char* e = std::getenv("PKR_TEST_SWITCH_TOL")) sw16 = sw32 = std::atof(e);
     int stages[3];
     double switch_tol[3];
     int nst = 0;
     if (p->precision == PKR_MIXED16) {
-        stages[nst] = PKR_FP16, switch_tol[nst++] = PKR_MIXED16_SWITCH_TOL;
-        stages[nst] = PKR_FP32, switch_tol[nst++] = PKR_MIXED_SWITCH_TOL;
+        stages[nst] = PKR_FP16, switch_tol[nst++] = sw16;
+        stages[nst] = PKR_FP32, switch_tol[nst++] = sw32;
         stages[nst] = PKR_FP64, switch_tol[nst++] = p->tol;
     } else if (p->precision == PKR_MIXED || p->precision == PKR_MIXED_FX64) {
-        stages[nst] = PKR_FP32, switch_tol[nst++] = PKR_MIXED_SWITCH_TOL;
+        stages[nst] = PKR_FP32, switch_tol[nst++] = sw32;
         stages[nst] = p->precision == PKR_MIXED ? PKR_FP64 : PKR_FX64, switch_tol[nst++] = p->tol;
     } else {
         stages[nst] = p->precision, switch_tol[nst++] = p->tol;
@@ -1016,6 +1029,7 @@ int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buf
             P = P2;
         }
         const bool last = (k == nst - 1);
+        if (!last) P->stall_cap = stages[k] == PKR_FP16 ? 0.1 : 1e-3;
         double t = switch_tol[k];
         if (!last && p->tol > t) t = p->tol;
         if (p->tol <= 0.0) t = 0.0;

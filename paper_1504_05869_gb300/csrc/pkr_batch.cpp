@@ -20,6 +20,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -184,6 +185,14 @@ struct pkr_ctx {
     double* h_mean = nullptr;  // pinned
     int64_t finished = 0, windows = 0;
     double site_updates = 0;
+    // non-threaded contexts: set while one thread runs a round (round()
+    // drops the lock while the windows run), so that no second thread
+    // drives the same lanes at the same time
+    bool driving = false;
+    // rounds that ran windows; a test may name one (environment variable
+    // PKR_TEST_FAIL_ROUND, read at creation) whose window launch then
+    // reports a CUDA error without launching anything
+    int64_t rounds = 0, fail_round = -1;
 };
 
 namespace {
@@ -669,8 +678,9 @@ int round(pkr_ctx* C, std::unique_lock<std::mutex>& lk)
         ran[ln] = true;
     }
     // the windows run without the lock so that submissions and polls proceed
+    const bool inject = C->rounds++ == C->fail_round;
     lk.unlock();
-    int rc = PKR_OK;
+    int rc = inject ? PKR_ECUDA : PKR_OK;
     for (int ln = 0; ln < C->nlanes && rc == PKR_OK; ++ln)
         if (ran[ln]) rc = launch_window(C, C->lane[ln]);
     if (rc == PKR_OK && cudaStreamSynchronize(C->stream) != cudaSuccess) rc = PKR_ECUDA;
@@ -688,14 +698,37 @@ int round(pkr_ctx* C, std::unique_lock<std::mutex>& lk)
     return 1;
 }
 
+// After a failed round: every live and queued request finishes with
+// PKR_ECUDA, and the live ones give their device memory (and their share of
+// the budget) back, so that a finished request holds nothing.  The stream is
+// drained first; after a sticky error nothing more runs on it anyway.
 void fail_all(pkr_ctx* C)
 {
+    cudaStreamSynchronize(C->stream);
     for (int ln = 0; ln < C->nlanes; ++ln) {
-        for (Job* j : C->lane[ln].live) finish(C, j, PKR_ECUDA);
+        for (Job* j : C->lane[ln].live) {
+            free_job_memory(C, j);
+            finish(C, j, PKR_ECUDA);
+        }
         C->lane[ln].live.clear();
+        C->lane[ln].dirty = true;
     }
-    for (Job* j : C->queue) finish(C, j, PKR_ECUDA);
+    for (Job* j : C->queue) finish(C, j, PKR_ECUDA);   // queued requests hold no memory
     C->queue.clear();
+    cudaStreamSynchronize(C->stream);
+    cudaGetLastError();
+}
+
+// One round of a non-threaded context, driven by the calling thread (the
+// caller holds the lock and has checked that no other thread drives).
+int drive_round(pkr_ctx* C, std::unique_lock<std::mutex>& lk)
+{
+    C->driving = true;
+    int r = round(C, lk);
+    if (r < 0) fail_all(C);
+    C->driving = false;
+    C->cv_done.notify_all();
+    return r;
 }
 
 void worker_main(pkr_ctx* C)
@@ -771,6 +804,7 @@ int pkr_ctx_create(const pkr_ctx_config* cfg, void* stream, pkr_ctx** out)
     C->budget = cfg->hbm_budget_bytes;
     C->max_grids = cfg->max_grids > 0 ? cfg->max_grids : 4096;
     C->mixed = cfg->precision == PKR_MIXED || cfg->precision == PKR_MIXED_FX64;
+    if (const char* fr = std::getenv("PKR_TEST_FAIL_ROUND")) C->fail_round = std::atoll(fr);
     C->nlanes = C->mixed ? 2 : 1;
     bool ok = cudaGetDevice(&C->device) == cudaSuccess &&
               cudaDeviceGetAttribute(&C->nsm, cudaDevAttrMultiProcessorCount, C->device) ==
@@ -879,14 +913,22 @@ int pkr_ctx_wait(pkr_ctx* C, uint64_t ticket, pkr_stats* st)
     if (it == C->jobs.end()) return PKR_EINVAL;
     Job* j = it->second;
     if (!C->cfg.threaded) {
+        // drive rounds until the request finishes; while another thread
+        // drives, wait for its round to end (the request stays registered as
+        // waited on, so that pkr_ctx_release cannot delete it meanwhile)
+        j->waiters += 1;
         while (j->status == PKR_EBUSY) {
-            int r = round(C, lk);
-            if (r < 0) {
-                fail_all(C);
-                return PKR_ECUDA;
+            if (C->driving) {
+                C->cv_done.wait(lk);
+                continue;
             }
-            if (r == 0 && j->status == PKR_EBUSY) return PKR_EINVAL;
+            const int r = drive_round(C, lk);
+            if (r == 0 && j->status == PKR_EBUSY) {
+                j->waiters -= 1;
+                return PKR_EINVAL;
+            }
         }
+        j->waiters -= 1;
     } else {
         j->waiters += 1;
         C->cv_done.wait(lk, [&] { return j->status != PKR_EBUSY || C->stop; });
@@ -902,7 +944,8 @@ int pkr_ctx_release(pkr_ctx* C, uint64_t ticket)
     auto it = C->jobs.find(ticket);
     if (it == C->jobs.end()) return PKR_EINVAL;
     Job* j = it->second;
-    // a finished request holds no device memory and sits in no queue or lane
+    // a finished request holds no device memory (retire and fail_all free
+    // it) and sits in no queue or lane
     if (j->status == PKR_EBUSY || j->waiters > 0) return PKR_EBUSY;
     C->jobs.erase(it);
     delete j;
@@ -915,11 +958,12 @@ int pkr_ctx_run(pkr_ctx* C, int64_t max_windows)
     std::unique_lock<std::mutex> lk(C->mu);
     int64_t n = 0;
     while (max_windows <= 0 || n < max_windows) {
-        int r = round(C, lk);
-        if (r < 0) {
-            fail_all(C);
-            return PKR_ECUDA;
+        if (C->driving) {   // another thread runs a round: wait for it to end
+            C->cv_done.wait(lk);
+            continue;
         }
+        const int r = drive_round(C, lk);
+        if (r < 0) return PKR_ECUDA;
         if (r == 0) break;
         ++n;
     }

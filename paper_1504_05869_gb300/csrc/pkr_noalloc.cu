@@ -3,13 +3,13 @@
 //
 // The regular path reduces the residual through per-block partial sums in a
 // scratch buffer that a plan allocates with cudaMalloc.  Some callers cannot
-// allocate: code running while a CUDA graph is being captured (an allocation
-// would break or be recorded into the capture), runtimes that own all device
-// memory through their own pool and forbid side allocations, and
-// latency-critical loops that must not touch the allocator.  For them this
-// file keeps the scratch in a file-scope static device array: every GPU that
-// loads the library holds these 24.6 KB until the process exits, and all calls
-// on a device share them.
+// allocate: runtimes that own all device memory through their own pool and
+// forbid side allocations, and latency-critical loops that must not enter the
+// allocator (cudaMalloc and cudaFree can synchronise the device).  For them
+// this file keeps the scratch in a file-scope static device array: every GPU
+// that loads the library holds these 24.6 KB until the process exits, and all
+// calls on a device share them.  A call ends by copying the three results to
+// the host and synchronising its stream.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -306,3 +306,123 @@ def test_batch_at_workload_sizes_sampled(pk, precision, bar):
     info = ctx.info()
     assert info["finished"] == len(grids) and info["bytes_in_use"] == 0
     ctx.close()
+
+
+def test_failed_round_frees_every_request(pk, monkeypatch):
+    """A round whose window launch fails (injected on the host: the context
+    reads PKR_TEST_FAIL_ROUND at creation and its round 1 reports a CUDA
+    error without launching anything) finishes every running and queued
+    request with PKR_ECUDA and gives their device memory back; their tickets
+    release cleanly, and the context serves the next request correctly."""
+    import torch
+    monkeypatch.setenv("PKR_TEST_FAIL_ROUND", "1")
+    ctx = pk.Context("D3Q111", 5, precision="fp32", check_every=8, hbm_budget_bytes=10 ** 9,
+                     max_grids=2)
+    monkeypatch.delenv("PKR_TEST_FAIL_ROUND")
+    subs = []
+    for seed, shape in ((31, (16, 16, 16)), (32, (12, 10, 14)), (33, (9, 7, 13))):
+        rho, _ = stiff_source(shape, count=3, sigma=1.5, seed=seed)
+        r = torch.from_numpy(rho).cuda()
+        phi = torch.zeros_like(r)
+        subs.append((ctx.submit(r, phi, tau_lb=1.3, tol=1e-7, max_sweeps=20000), r, phi))
+    with pytest.raises(pk.PkrError) as e:
+        ctx.run()     # round 0 runs two live requests (max_grids 2), round 1 fails
+    assert e.value.status == pk._pkr.PKR_ECUDA
+    for t, _, _ in subs:
+        rc, st = ctx.poll(t)
+        assert rc == pk._pkr.PKR_ECUDA
+        assert ctx.release(t) == 0
+    info = ctx.info()
+    assert info["bytes_in_use"] == 0 and info["finished"] == 3
+    rho, _ = stiff_source((16, 16, 16), count=3, sigma=1.5, seed=34)
+    r = torch.from_numpy(rho).cuda()
+    phi = torch.zeros_like(r)
+    t = ctx.submit(r, phi, tau_lb=1.3, tol=1e-7, max_sweeps=20000)
+    ctx.run()
+    rc, st = ctx.poll(t)
+    assert rc == 0
+    ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.3, max_steps=st["sweeps"]).phi
+    assert _rel(phi.cpu().numpy(), ref) <= 2e-5
+    assert ctx.info()["bytes_in_use"] == 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fx64", "mixed"])
+def test_request_joining_a_running_batch(pk, precision):
+    """Continuous batching: request A runs for three windows, then B arrives
+    and is admitted into the live batch; both finish together.  Each result
+    equals (bit for bit) the same request run alone, and so does its sweep
+    count."""
+    import torch
+    K = 8
+
+    def job(seed, shape, tau, tol):
+        rho, _ = stiff_source(shape, count=4, sigma=1.5, seed=seed)
+        return rho, dict(tau_lb=tau, tol=tol, tol_kind="rel_l2", max_sweeps=20000)
+
+    A = job(51, (16, 14, 12), 1.3, 1e-9 if precision != "fp32" else 1e-7)
+    B = job(52, (12, 18, 10), 2.0, 1e-8 if precision != "fp32" else 1e-7)
+
+    def alone(rho, kw):
+        ctx = pk.Context("D3Q111", 5, precision=precision, check_every=K,
+                         hbm_budget_bytes=2 * 10 ** 9)
+        r = torch.from_numpy(rho).cuda()
+        phi = torch.zeros_like(r)
+        t = ctx.submit(r, phi, **kw)
+        ctx.run()
+        rc, st = ctx.poll(t)
+        ctx.close()
+        return rc, st, phi.cpu().numpy()
+
+    ctx = pk.Context("D3Q111", 5, precision=precision, check_every=K, hbm_budget_bytes=2 * 10 ** 9)
+    ra = torch.from_numpy(A[0]).cuda()
+    pa = torch.zeros_like(ra)
+    ta = ctx.submit(ra, pa, **A[1])
+    ctx.run(max_windows=3)
+    assert ctx.poll(ta)[0] == pk._pkr.PKR_EBUSY            # A is still running
+    rb = torch.from_numpy(B[0]).cuda()
+    pb = torch.zeros_like(rb)
+    tb = ctx.submit(rb, pb, **B[1])                        # B joins the live batch
+    ctx.run(max_windows=1)
+    assert ctx.poll(ta)[0] == pk._pkr.PKR_EBUSY and ctx.poll(tb)[0] == pk._pkr.PKR_EBUSY
+    assert ctx.info()["bytes_in_use"] > 0
+    ctx.run()
+    (rca, sta), (rcb, stb) = ctx.poll(ta), ctx.poll(tb)
+    ctx.close()
+    for (rc, st, got), ref in (((rca, sta, pa.cpu().numpy()), alone(*A)),
+                               ((rcb, stb, pb.cpu().numpy()), alone(*B))):
+        assert rc == 0 and ref[0] == 0
+        assert st["sweeps"] == ref[1]["sweeps"]
+        assert np.array_equal(got, ref[2])
+
+
+def test_two_threads_drive_one_context(pk):
+    """Two host threads wait on different requests of one non-threaded
+    context at the same time: one drives each round while the other waits for
+    it, and both results equal the oracle's."""
+    import threading
+    import torch
+    ctx = pk.Context("D3Q111", 5, precision="fp64", check_every=8, hbm_budget_bytes=2 * 10 ** 9)
+    subs = []
+    for seed, shape, tau in ((61, (12, 10, 14), 1.3), (62, (9, 7, 13), 2.0)):
+        rho, _ = stiff_source(shape, count=3, sigma=1.5, seed=seed)
+        r = torch.from_numpy(rho).cuda()
+        phi = torch.zeros_like(r)
+        subs.append((rho, tau, r, phi, ctx.submit(r, phi, tau_lb=tau, tol=1e-9,
+                                                   max_sweeps=20000)))
+    out = [None, None]
+
+    def waiter(k):
+        out[k] = ctx.wait(subs[k][4])
+
+    th = [threading.Thread(target=waiter, args=(k,)) for k in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join(timeout=300)
+    assert all(o is not None for o in out)
+    for (rho, tau, r, phi, t), (rc, st) in zip(subs, out):
+        assert rc == 0
+        ref = oracle.solve(rho, "D3Q111", 5, tau_lb=tau, max_steps=st["sweeps"]).phi
+        assert _rel(phi.cpu().numpy(), ref) <= 1e-12
+    ctx.close()

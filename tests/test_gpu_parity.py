@@ -572,3 +572,23 @@ def test_per_step_checks_in_captured_graphs(pk, lattice, order, shape, tau):
         host = P.phi(torch.empty_like(r)).cpu().numpy()
         assert P.steps() == st["sweeps"]
     assert np.array_equal(host, got)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_fx64", "mixed16"])
+def test_ladder_hands_over_at_the_rounding_floor(pk, monkeypatch, precision):
+    """With switch tolerances no reduced-precision storage can reach
+    (PKR_TEST_SWITCH_TOL=1e-14), each reduced-precision rung of pkr_solve's
+    ladder stalls at its rounding floor and hands over once its residual stops
+    falling; the solve still converges to tol, far below max_sweeps, as close
+    to the binary64 fixed point as a binary64 solve."""
+    monkeypatch.setenv("PKR_TEST_SWITCH_TOL", "1e-14")
+    shape = (12, 10, 14)
+    rho, _ = stiff_source(shape, count=6, sigma=1.5, seed=16)
+    star = oracle.solve(rho, "D3Q111", 5, tau_lb=1.3, tol=1e-15, tol_kind=1,
+                        check_every=8, max_steps=400000).phi
+    got, rc, st = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-12, precision=precision,
+                             max_sweeps=400000)
+    g64, rc64, st64 = _gpu_solve(pk, rho, "D3Q111", 5, 1.3, tol=1e-12, max_sweeps=400000)
+    assert rc == 0 and rc64 == 0 and st["residual"] < 1e-12
+    assert st["sweeps"] < 3 * st64["sweeps"]
+    assert _rel(got, star) < 5e-9 and _rel(g64, star) < 5e-9
