@@ -10,9 +10,20 @@ GB) are far larger than L2, so no flush is needed between steps.
 
 ``e2e``: the same metric for a complete solve to rel. residual 1e-10 through
 ``pkr_solve`` with host buffers (H2D of rho and D2H of Phi inside the timed
-region).  ``cpu_baseline``: the oracle (serial C) on a 64-plane slab of the same
+region).  ``cpu_baseline``: the oracle (serial C) on a 16-plane slab of the same
 source; ``cpu_baseline_openmp``: the same source built with OpenMP on every host
-core.  ``--impl reference`` times the serial oracle alone, as the reference arm.
+core; ``cpu_full_solve``: the oracle's whole 2D 64^2 D2Q169 solve (serial and
+OpenMP) beside the GPU's.  ``--impl reference`` times the serial oracle alone on
+the same slab, as the reference arm.
+
+Two more of the reference's metrics ride on the same line (single GPU only,
+after the timed region; the headline value is the sweep's):
+``time_to_1e8``: the exact fixed point by the FFT comparator, then the plain
+binary64 solve (the e2e solve above) against the MIXED and MIXED_FX64 ladders,
+each to rel. residual 1e-10, with each result's rel. L2 distance to the fixed
+point (all ~7e-9); ``serving``: the serving trace (Poisson arrivals of 3D
+solves, edges 32-256, tolerances 1e-6/1e-8/1e-10) at 200/s and at a
+sub-capacity rate, with solves/s and p50/p99 latency.
 
 Multi-GPU: the path does not shard (one grid per GPU, no collectives), so N
 ranks run N independent replicas; value = all ranks' site updates / the
@@ -38,8 +49,7 @@ LATTICE, ORDER, KN = "D3Q111", 5, 0.2
 PRECISION = "fp64"
 TAU = 0.0            # > 0: tau_lb directly instead of the Knudsen number
 SWEEPS_PER_STEP = 32
-SLAB = 64            # planes of the CPU-baseline sample
-REF_SLAB = 2         # planes per reference-arm step
+SLAB = 16            # planes of the CPU-baseline sample (the reference arm's step too)
 METRIC = "GLUPS (site updates/s, 1e9) of the fused sweep"
 WORKLOAD = "poisson3d_256cube_d3q111_n5_fp64_64gauss_sigma2_seed0_kn0.2"
 
@@ -177,9 +187,83 @@ def cpu_baseline_openmp(rho, tau):
             "sample": f"1 step on the same {SLAB}x256x256 slab, {cores} threads, {dt:.2f} s"}
 
 
+def cpu_full_solve(pk, torch):
+    """A whole solve on the host's cores: the 2D 64^2 problem (D2Q169 N=7,
+    rho = sin(2 pi x/64) sin(2 pi y/64), Kn 0.1, stop at max|dPhi| < 1e-12),
+    serial and with the OpenMP build, beside the same solve on the GPU.  A
+    reported baseline only."""
+    import oracle
+    from paper_1504_05869_gb300.workloads import sinusoid
+    rho = sinusoid((64, 64))
+    out = {"problem": "64^2 D2Q169 N=7, Kn 0.1, max|dPhi| < 1e-12 (every step)"}
+    t0 = time.perf_counter()
+    ref = oracle.solve(rho, "D2Q169", 7, knudsen=0.1, tol=1e-12, tol_kind=0, check_every=1,
+                       max_steps=100000)
+    out["serial"] = {"seconds": time.perf_counter() - t0, "steps": ref.steps, "cores": 1}
+    try:
+        cores = oracle.threads(len(os.sched_getaffinity(0)))
+        t0 = time.perf_counter()
+        ro = oracle.solve(rho, "D2Q169", 7, knudsen=0.1, tol=1e-12, tol_kind=0, check_every=1,
+                          max_steps=100000, openmp=True)
+        out["openmp"] = {"seconds": time.perf_counter() - t0, "steps": ro.steps, "cores": cores}
+    except Exception as e:              # no OpenMP-capable compiler on this host
+        out["openmp"] = {"unavailable": f"{e}"[:200]}
+    r = torch.from_numpy(rho).cuda()
+    phi = torch.empty_like(r)
+    prob = pk.problem("D2Q169", (64, 64), 7, knudsen=0.1, tol=1e-12, tol_kind="max_abs",
+                      check_every=1, max_sweeps=100000)
+    pk.solve(r, phi, prob)               # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, st = pk.solve(r, phi, prob)
+    torch.cuda.synchronize()
+    out["gpu"] = {"seconds": time.perf_counter() - t0, "steps": st["sweeps"], "status": rc}
+    return out
+
+
+def time_to_1e8(pk, torch, r, phi64, solve64, stream):
+    """Time to a solution within ~1e-8 (rel. L2) of the scheme's exact
+    binary64 fixed point at 256^3: the FFT comparator gives the fixed point
+    itself; the plain binary64 solve (the e2e solve, host buffers) and the
+    MIXED / MIXED_FX64 ladders (binary32 steps, then binary64 or 64-bit fixed
+    point from the converted state) each run to rel. residual 1e-10."""
+    ref = torch.empty_like(r)
+    prob = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN)
+    pk.fixed_point_fft(r, ref, prob)                 # warm-up (cuFFT plans)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pk.fixed_point_fft(r, ref, prob)
+    torch.cuda.synchronize()
+    out = {"fixed_point_fft_s": time.perf_counter() - t0}
+    nref = torch.linalg.norm(ref).item()
+    out["fp64"] = {"seconds": solve64["seconds"], "sweeps": solve64["sweeps"],
+                   "status": solve64["status"],
+                   "rel_l2_vs_fixed_point": torch.linalg.norm(phi64 - ref).item() / nref}
+    for prec in ("mixed", "mixed_fx64"):
+        phi = torch.empty_like(r)
+        p = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN, tol=1e-10, tol_kind="rel_l2",
+                       check_every=SWEEPS_PER_STEP, max_sweeps=200000, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            rc, st = pk.solve(r, phi, p, stream=stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[prec] = {"seconds": dt, "sweeps": st["sweeps"], "status": rc,
+                     "rel_l2_vs_fixed_point": torch.linalg.norm(phi - ref).item() / nref,
+                     "speedup_vs_fp64": solve64["seconds"] / dt}
+        del phi
+    del ref
+    torch.cuda.empty_cache()
+    out["note"] = ("each run to rel. residual 1e-10; the fp64 time is the e2e solve "
+                   "(host buffers, copies included)")
+    return out
+
+
 def run_reference(args):
     """Reference arm: the oracle timed on the host, each step one oracle step
-    on a 2-plane slab of the benchmark's source."""
+    on the 16-plane slab of the benchmark's source that the GPU line's
+    cpu_baseline times."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -187,7 +271,7 @@ def run_reference(args):
     rho = source()
     lat = oracle.lattice(LATTICE, ORDER)
     tau = oracle.tau_from_knudsen(KN, SHAPE[::-1], lat.cs2)
-    slab = np.ascontiguousarray(rho[:REF_SLAB])
+    slab = np.ascontiguousarray(rho[:SLAB])
     for _ in range(args.warmup):
         oracle.solve(slab, LATTICE, ORDER, tau_lb=tau, max_steps=1)
     t0 = time.perf_counter()
@@ -199,10 +283,11 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"{REF_SLAB}x256x256 slab, 1 step"},
+            "config": {"workload": WORKLOAD, "sample": f"{SLAB}x256x256 slab, 1 step"},
             "cpu_baseline": {"value": val, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"one oracle step on a {REF_SLAB}x256x256 slab per "
-                                       "benchmark step"},
+                             "sample": f"one oracle step on a {SLAB}x256x256 slab per "
+                                       "benchmark step (the slab of the GPU line's "
+                                       "cpu_baseline)"},
             "e2e": {"value": val, "unit": "GLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -306,10 +391,21 @@ def run(args):
                "solve": {"sweeps": est["sweeps"], "residual": est["residual"],
                          "status": rc, "seconds": e_s, "tol": 1e-10}}
 
-    cpu = cpu_omp = None
+    # the reference's other two metrics, on one GPU, after the timed region
+    t2e8 = serving = None
+    if world == 1 and not args.no_extras and e2e is not None and PRECISION == "fp64" \
+            and TAU == 0.0:
+        t2e8 = time_to_1e8(pk, torch, r_dev, phi_h.cuda(),
+                           e2e["solve"], stream)
+        serving = {"overloaded": serve_trace(pk, args.serve_requests, 200.0, "mixed", 150.0),
+                   "sub_capacity": serve_trace(pk, args.serve_sub_requests,
+                                               args.serve_sub_rate, "mixed", 150.0)}
+
+    cpu = cpu_omp = cpu_full = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(rho, tau)
         cpu_omp = cpu_baseline_openmp(rho, tau)
+        cpu_full = cpu_full_solve(pk, torch)
 
     if stencil:
         # binary64 FMA bound: Q FMAs per site; peak from the GB300's nominal
@@ -343,7 +439,8 @@ def run(args):
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs": V * bytes_site * sweeps * world / (dev_ms * 1e-3) / 1e9,
             "roofline": roofline,
-            "cpu_baseline": cpu, "cpu_baseline_openmp": cpu_omp, "e2e": e2e,
+            "cpu_baseline": cpu, "cpu_baseline_openmp": cpu_omp, "cpu_full_solve": cpu_full,
+            "e2e": e2e, "time_to_1e8": t2e8, "serving": serving,
             "clocks": clocks, "gpu_launches": args.steps * (SWEEPS_PER_STEP + 1),
             "wall_s": wall,
         }
@@ -416,23 +513,21 @@ def run_batch(args):
     return 0
 
 
-def run_serve(args):
-    """Poisson arrivals (seed 3) of periodic 3D solves, edges log-uniform in
-    [32, 256], tolerances from {1e-6, 1e-8, 1e-10}, smooth/stiff mix,
-    continuous batching under an HBM budget; latency = completion - arrival."""
+def serve_trace(pk, count, rate, precision, budget_gb):
+    """Serve the first `count` requests of the seed-3 arrival trace at `rate`
+    per second through a threaded context (continuous batching under an HBM
+    budget; requests are submitted at their arrival times, host-side inputs
+    prepared beforehand).  Latency = completion - submission."""
     import threading as th
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_1504_05869_gb300 as pk
     from paper_1504_05869_gb300.workloads import serving_trace
-    trace = serving_trace(args.requests, rate_hz=args.rate, seed=3)
+    trace = serving_trace(count, rate_hz=rate, seed=3)
     rhos = [torch.from_numpy(rq.rho()).cuda() for rq in trace]
     phis = [torch.zeros_like(r) for r in rhos]
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()
-    ctx = pk.Context("D3Q111", 5, precision=args.precision, check_every=SWEEPS_PER_STEP,
-                     hbm_budget_bytes=int(args.budget_gb * 1e9), variant=-1, threaded=True,
+    ctx = pk.Context("D3Q111", 5, precision=precision, check_every=SWEEPS_PER_STEP,
+                     hbm_budget_bytes=int(budget_gb * 1e9), variant=-1, threaded=True,
                      stream=stream)
     tickets = [None] * len(trace)
     t0 = time.perf_counter()
@@ -454,18 +549,33 @@ def run_serve(args):
         rcs.append(rc)
         lat.append(st["wall_ms"] / 1e3)
         sw.append(st["sweeps"])
+        ctx.release(t)
     dt = time.perf_counter() - t0
     info = ctx.info()
     ctx.close()
+    del rhos, phis
+    torch.cuda.empty_cache()
     offered = len(trace) / max(trace[-1].arrival_s, 1e-9)
-    line = {"metric": "served solves/s with p50/p99 latency", "workload": "serve",
-            "value": len(trace) / dt, "unit": "solves/s",
-            "p50_latency_s": _pct(lat, 50), "p99_latency_s": _pct(lat, 99),
+    return {"solves_per_s": len(trace) / dt, "p50_latency_s": _pct(lat, 50),
+            "p99_latency_s": _pct(lat, 99), "max_latency_s": max(lat),
             "offered_rate_hz": offered, "requests": len(trace), "seconds": dt,
             "ok": sum(1 for r in rcs if r == 0), "statuses": sorted(set(rcs)),
-            "glups": info["site_updates"] / dt / 1e9, "precision": args.precision,
-            "hbm_budget_gb": args.budget_gb, "check_every": SWEEPS_PER_STEP,
-            "data": "synthetic",
+            "glups": info["site_updates"] / dt / 1e9, "precision": precision,
+            "sweeps_median": _pct(sw, 50), "hbm_budget_gb": budget_gb,
+            "trace": f"first {len(trace)} arrivals of the seed-3 Poisson trace at {rate:g}/s"}
+
+
+def run_serve(args):
+    """Poisson arrivals (seed 3) of periodic 3D solves, edges log-uniform in
+    [32, 256], tolerances from {1e-6, 1e-8, 1e-10}, smooth/stiff mix,
+    continuous batching under an HBM budget; latency = completion - arrival."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+    r = serve_trace(pk, args.requests, args.rate, args.precision, args.budget_gb)
+    line = {"metric": "served solves/s with p50/p99 latency", "workload": "serve",
+            "value": r["solves_per_s"], "unit": "solves/s", **r,
+            "check_every": SWEEPS_PER_STEP, "data": "synthetic",
             "config": {"arrivals": f"Poisson {args.rate}/s, seed 3", "edges": "[32,256]",
                        "tols": [1e-6, 1e-8, 1e-10], "lattice": "D3Q111", "knudsen": KN}}
     print(json.dumps(line), flush=True)
@@ -825,6 +935,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pkr", choices=["pkr", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the time-to-1e-8 and serving objects of the default line")
+    ap.add_argument("--serve-requests", type=int, default=500,
+                    help="default line: arrivals of the 200/s serving trace")
+    ap.add_argument("--serve-sub-requests", type=int, default=16)
+    ap.add_argument("--serve-sub-rate", type=float, default=1.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--size", type=int, default=0, help="cube edge (default 256)")
     ap.add_argument("--lattice", default="D3Q111", choices=["D3Q111", "D3Q19"])

@@ -81,12 +81,12 @@ typedef enum pkr_lattice {
  * arithmetic in binary32, source in binary32; accurate to ~1e-4 of Phi.
  * MIXED16 (pkr_solve only): binary16 to PKR_MIXED16_SWITCH_TOL, binary32 to
  * PKR_MIXED_SWITCH_TOL, then binary64 to tol.
- * In pkr_solve's ladders (and in contexts) a reduced-precision rung also
- * hands over when its per-step change stops falling from one check to the
- * next (from the third check on, and below 0.1 for binary16, 1e-3 for
- * binary32): its rounding floor can lie above the switch tolerance.  (Tests
- * can set both switch tolerances of pkr_solve with the environment variable
- * PKR_TEST_SWITCH_TOL.)
+ * A reduced-precision rung also hands over at its rounding floor, which can
+ * lie above the switch tolerance: in pkr_solve's ladders when four checks in
+ * a row bring no new smallest per-step change (below 0.1 for binary16, 1e-3
+ * for binary32); in contexts when the change stops falling from one check to
+ * the next (below 1e-3).  (Tests can set both switch tolerances of pkr_solve
+ * with the environment variable PKR_TEST_SWITCH_TOL.)
  * FX64: populations stored as 64-bit integers v 2^F with a power-of-two scale
  * per array (F lowered on the device whenever the largest stored value
  * passes 2^54).  The density is an exact integer sum and the relaxation a

@@ -352,6 +352,10 @@ int set_variant(pkr_plan* P, int variant)
     return PKR_OK;
 }
 
+// Checks without a new smallest residual after which a reduced-precision rung
+// of pkr_solve's ladder is taken to sit at its rounding floor.
+constexpr int kStallChecks = 4;
+
 // Steps per captured graph of device-stopped check steps (even, so that the
 // arrays are back at the same parity after a full replay).
 constexpr int kGraphSteps = 64;
@@ -861,8 +865,8 @@ int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check
     const int64_t K = check_every > 0 ? check_every : P->prob.check_every;
     const double t0 = now_ms();
     int status = PKR_OK;
-    double min_res = INFINITY, prev_res = INFINITY;
-    int nchecks = 0;
+    double min_res = INFINITY;
+    int nchecks = 0, since_min = 0;   // checks since the last new minimum
     int64_t done = 0;
     bool stopped = false;
     // Binary64 runs that check every step (the per-step stopping rules of
@@ -935,10 +939,13 @@ int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check
                 status = PKR_EDIVERGED;
                 break;
             }
+            since_min = r < min_res ? 0 : since_min + 1;
             if (r < min_res) min_res = r;
             if (tol > 0.0 && r < tol) break;
-            if (P->stall_cap > 0.0 && nchecks > 2 && r >= prev_res && r < P->stall_cap) break;
-            prev_res = r;
+            // a reduced-precision rung at its rounding floor: no new minimum
+            // for kStallChecks checks in a row (the residual of a converging
+            // run may rise for a check or two on its way down)
+            if (P->stall_cap > 0.0 && since_min >= kStallChecks && r < P->stall_cap) break;
         }
     }
     PKR_CK(cudaStreamSynchronize(P->stream));

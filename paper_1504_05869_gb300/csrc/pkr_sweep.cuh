@@ -345,7 +345,10 @@ __device__ __forceinline__ double pow2(int e)
 }
 
 // The part of a tile step that follows the pull, for velocity group g of G
-// (velocities lo(g) .. lo(g + 1) - 1): the group's share of the density
+// (velocities lo(g) .. lo(g + 1) - 1), as the warp-specialised sweep runs it;
+// tile_step below carries the same operations inline (its binary64 sweep
+// measured 1.9% slower when it called this function instead): the group's
+// share of the density
 // (the G warps of a tile meet at named barrier `bar`, twice in binary64 and
 // once otherwise; every meeting sits outside lane-dependent branches), the
 // relaxation and store of the group's velocities, and, in group 0, the
@@ -510,8 +513,11 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
     using ST = Staged<L, T, G, TILES>;
     constexpr int RC = reach_of<L>();
     constexpr int W = 2 * RC + 1;
-    static_assert(63 - 53 - ceil_log2(L::Q) >= 1, "too many velocities for the 64-bit density sum");
+    constexpr int NC = ncls_of<L>();
+    constexpr int GB = 63 - 53 - ceil_log2(L::Q);
+    static_assert(GB >= 1, "too many velocities for the 64-bit density sum");
     const T* __restrict__ A = tg.A;
+    T* __restrict__ B = tg.B;
     const int64_t V = tg.V;
     const int nx = tg.nx, ny = tg.ny, nz = tg.nz;
     const int nxy = nx * ny;
@@ -551,6 +557,7 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
         constexpr int g = decltype(GI)::value;
         constexpr int lo = ST::lo(g);
         constexpr int hi = ST::lo(g + 1);
+        constexpr int n = hi - lo;
         if (grp != g) return;
         // pull: one asynchronous copy per velocity of this group
         static_for<lo, hi>([&](auto I) {
@@ -563,8 +570,131 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
         });
         cp_async_wait_all();
 
-        group_compute<L, T, G, g>(tg, c, mode, valid, s, Sx, lane, sbase, 1 + sub, xacc[sub],
-                                  xexp[sub], d2, n2, mx, ms, fxm);
+        // density (the G warps of a tile meet twice at named barrier 1 + sub;
+        // both barriers sit outside every lane-dependent branch)
+        R Phi;
+        if constexpr (std::is_same<T, long long>::value) {
+            // fixed point: the density is an exact integer sum
+            long long part = 0;
+#pragma unroll 8
+            for (int k = 0; k < n; ++k) part += lds_s64(sbase + k * 256);
+            if constexpr (G > 1) {
+                xacc[sub][g][lane] = part;
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+                part = 0;
+#pragma unroll
+                for (int k = 0; k < G; ++k) part += xacc[sub][k][lane];
+            }
+            Phi = (double)part * pow2(-tg.fr);
+        } else if constexpr (std::is_same<T, double>::value) {
+            int emax = max_exponent<n>(sbase);
+            if constexpr (G > 1) {
+                xexp[sub][g][lane] = emax;
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+#pragma unroll
+                for (int k = 0; k < G; ++k) emax = max(emax, xexp[sub][k][lane]);
+            }
+            const bool plain = plain_path(emax);
+            long long part = plain ? __double_as_longlong(plain_sum<n>(sbase))
+                                   : fixed_sum<GB, n>(sbase, emax);
+            if constexpr (G > 1) {
+                xacc[sub][g][lane] = part;
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+                if (plain) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int k = 0; k < G; ++k) t += __longlong_as_double(xacc[sub][k][lane]);
+                    Phi = t;
+                } else {
+                    long long t = 0;
+#pragma unroll
+                    for (int k = 0; k < G; ++k) t += xacc[sub][k][lane];
+                    Phi = fixed_value<GB>(t, emax);
+                }
+            } else {
+                Phi = plain ? __longlong_as_double(part) : fixed_value<GB>(part, emax);
+            }
+        } else {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 2
+            for (int k = 0; k + 3 < n; k += 4) {
+                s0 += lds_f32(sbase + (k + 0) * 128);
+                s1 += lds_f32(sbase + (k + 1) * 128);
+                s2 += lds_f32(sbase + (k + 2) * 128);
+                s3 += lds_f32(sbase + (k + 3) * 128);
+            }
+#pragma unroll
+            for (int k = n - n % 4; k < n; ++k) s0 += lds_f32(sbase + k * 128);
+            float part = (s0 + s1) + (s2 + s3);
+            if constexpr (G > 1) {
+                // binary32 partials meet in group order (fixed, deterministic)
+                xacc[sub][g][lane] = (long long)__float_as_int(part);
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
+                part = 0.f;
+#pragma unroll
+                for (int k = 0; k < G; ++k) part += __int_as_float((int)xacc[sub][k][lane]);
+            }
+            Phi = part;
+        }
+
+        // relax and store this group's velocities, one symmetry class at a
+        // time (velocities of a class are contiguous and share phi_c, chi_c)
+        if (valid) {
+            static_for<0, NC>([&](auto CI) {
+                constexpr int cl = decltype(CI)::value;
+                constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
+                constexpr int i0 = cb > lo ? cb : lo;
+                constexpr int i1 = ce < hi ? ce : hi;
+                if constexpr (i0 < i1 && std::is_same<T, long long>::value) {
+                    const double e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
+                    const long long ei = __double2ll_rn(e * pow2(tg.fw));
+                    // the written array's scale is 2^-k that of the read one (k >= 0,
+                    // the rescale only lowers it): fold 2^-k into the coefficient
+                    const int k = tg.fr - tg.fw;
+                    const long long cw = k == 0 ? tg.cfx : ((tg.cfx >> (k - 1)) + 1) >> 1;
+                    T* dst = B + ((int64_t)i0 * V + s);
+#pragma unroll 4
+                    for (int i = i0; i < i1; ++i) {
+                        const long long p = fx_mul(lds_s64(sbase + (i - lo) * 256), cw) + ei;
+                        fxm |= (unsigned long long)(p ^ (p >> 63));
+                        store_stream(dst, (T)p);
+                        dst += V;
+                    }
+                } else if constexpr (i0 < i1) {
+                    const R e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
+                    T* dst = B + ((int64_t)i0 * V + s);
+                    int i = i0;
+                    for (; i + 3 < i1; i += 4) {
+                        const R g0 = lds_val<T>(sbase + (i + 0 - lo) * 32 * sizeof(T));
+                        const R g1 = lds_val<T>(sbase + (i + 1 - lo) * 32 * sizeof(T));
+                        const R g2 = lds_val<T>(sbase + (i + 2 - lo) * 32 * sizeof(T));
+                        const R g3 = lds_val<T>(sbase + (i + 3 - lo) * 32 * sizeof(T));
+                        store_stream(dst, (T)fma(c.om1, g0, e));
+                        store_stream(dst + V, (T)fma(c.om1, g1, e));
+                        store_stream(dst + 2 * V, (T)fma(c.om1, g2, e));
+                        store_stream(dst + 3 * V, (T)fma(c.om1, g3, e));
+                        dst += 4 * V;
+                    }
+                    for (; i < i1; ++i) {
+                        const R gi = lds_val<T>(sbase + (i - lo) * 32 * sizeof(T));
+                        store_stream(dst, (T)fma(c.om1, gi, e));
+                        dst += V;
+                    }
+                }
+            });
+        }
+        // density output and residual contributions (one group per tile)
+        if (g == 0 && mode != kPlain && valid) {
+            const double ph = (double)Phi;
+            if (mode == kCheck) {
+                const double d = ph - tg.Phi[s];
+                d2 += d * d;
+                n2 += ph * ph;
+                mx = fmax(mx, fabs(d));
+                ms += ph;
+            }
+            tg.Phi[s] = ph;
+        }
     });
     __syncwarp();
 }
