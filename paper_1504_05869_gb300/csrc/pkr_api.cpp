@@ -499,7 +499,12 @@ int pkr_plan_bytes(const pkr_problem* p, size_t* bytes)
     return PKR_OK;
 }
 
-int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
+namespace {
+
+// pkr_plan_create, with the second population array optional (spare =
+// false: only pop[0] is allocated, for a ladder rung that receives a
+// converted state in pop[0] and gets pop[1] once the previous rung is gone).
+int plan_create(const pkr_problem* p, void* stream, pkr_plan** out, bool spare)
 {
     if (!out) return PKR_EINVAL;
     *out = nullptr;
@@ -576,7 +581,7 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
         return PKR_ECUDA;
     }
     const size_t need = P->stencil ? (size_t)P->V * 8 * 5 + (size_t)4 * kMaxGridBlocks * 8
-                                   : plan_bytes(p, li, P->V, kMaxGridBlocks);
+                                   : plan_bytes(p, li, P->V, kMaxGridBlocks) - (spare ? 0 : popb);
     if (need > freeb) {
         delete P;
         return PKR_ENOMEM;
@@ -587,7 +592,7 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
                       cudaMalloc((void**)&P->Ps[1], (size_t)P->V * 8) == cudaSuccess &&
                       cudaMalloc((void**)&P->St, (size_t)P->V * 8) == cudaSuccess)
                    : (cudaMalloc(&P->pop[0], popb) == cudaSuccess &&
-                      cudaMalloc(&P->pop[1], popb) == cudaSuccess)) &&
+                      (!spare || cudaMalloc(&P->pop[1], popb) == cudaSuccess))) &&
               cudaMalloc(&P->S, (size_t)P->V * source_bytes(p->precision)) == cudaSuccess &&
               cudaMalloc((void**)&P->h16sc, 2 * sizeof(float)) == cudaSuccess &&
               cudaMalloc((void**)&P->h16max, sizeof(unsigned int)) == cudaSuccess &&
@@ -607,6 +612,38 @@ int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
     if (P->stencil) P->Phi = P->Ps[0];
     *out = P;
     return PKR_OK;
+}
+
+size_t pop_bytes(const pkr_plan* P)
+{
+    return (size_t)P->lat.Q * (size_t)P->V * (size_t)P->elem + 16;
+}
+
+// Free the population array a plan does not read next (its state stays in
+// pop[cur], Phi and S; it cannot step again until plan_alloc_spare).
+void plan_free_spare(pkr_plan* P)
+{
+    if (P->stencil || !P->pop[P->cur ^ 1]) return;
+    cudaStreamSynchronize(P->stream);
+    cudaFree(P->pop[P->cur ^ 1]);
+    P->pop[P->cur ^ 1] = nullptr;
+}
+
+int plan_alloc_spare(pkr_plan* P)
+{
+    if (P->stencil || P->pop[P->cur ^ 1]) return PKR_OK;
+    if (cudaMalloc(&P->pop[P->cur ^ 1], pop_bytes(P)) != cudaSuccess) {
+        cudaGetLastError();
+        return PKR_ENOMEM;
+    }
+    return PKR_OK;
+}
+
+}  // namespace
+
+int pkr_plan_create(const pkr_problem* p, void* stream, pkr_plan** out)
+{
+    return plan_create(p, stream, out, true);
 }
 
 int pkr_plan_destroy(pkr_plan* P)
@@ -637,7 +674,12 @@ int pkr_plan_destroy(pkr_plan* P)
     return PKR_OK;
 }
 
-int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
+namespace {
+
+// pkr_plan_load_source; first_step = false leaves out the first step (from
+// zero populations), for a plan that pkr_plan_import fills next: it touches
+// pop[0] only.
+int load_source(pkr_plan* P, const double* rho, int rho_on_host, bool first_step)
 {
     if (!P || !rho) return PKR_EINVAL;
     const double* rd = rho;
@@ -720,10 +762,21 @@ int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
     P->cur = 0;
     P->last_residual = -1.0;
     P->soff_next = 0.0;
-    int rc = launch_one(P, kWritePhi, true);
-    if (rc != PKR_OK) return rc;
+    if (first_step) {
+        int rc = launch_one(P, kWritePhi, true);
+        if (rc != PKR_OK) return rc;
+    } else {
+        PKR_CK(cudaStreamSynchronize(P->stream));
+    }
     P->loaded = true;
     return PKR_OK;
+}
+
+}  // namespace
+
+int pkr_plan_load_source(pkr_plan* P, const double* rho, int rho_on_host)
+{
+    return load_source(P, rho, rho_on_host, true);
 }
 
 int pkr_variant_count(int lattice) { return variant_count(lattice); }
@@ -1022,11 +1075,18 @@ int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buf
     int64_t prev_launches = 0;
     for (int k = 0; k < nst; ++k) {
         if (k > 0) {
+            // Hand the state on with little memory: the rung's second array
+            // goes first, the next rung is built with one array, receives
+            // the converted state in it, and gets its second array once the
+            // previous rung is gone.  Peak: the rung's state + one array of
+            // the next (binary32 to binary64 at 512^3: 60 + 119 GB; then the
+            // two binary64 arrays, 238 GB).
             pkr_problem pk = *p;
             pk.precision = stages[k];
+            plan_free_spare(P);
             pkr_plan* P2 = nullptr;
-            rc = pkr_plan_create(&pk, stream, &P2);
-            if (rc == PKR_OK) rc = pkr_plan_load_source(P2, rho, host_buffers);
+            rc = plan_create(&pk, stream, &P2, false);
+            if (rc == PKR_OK) rc = load_source(P2, rho, host_buffers, false);
             if (rc == PKR_OK) rc = pkr_plan_import(P2, P);
             if (rc != PKR_OK) {
                 if (P2) pkr_plan_destroy(P2);
@@ -1034,6 +1094,8 @@ int pkr_solve(const pkr_problem* p, const double* rho, double* phi, int host_buf
             }
             pkr_plan_destroy(P);
             P = P2;
+            rc = plan_alloc_spare(P);
+            if (rc != PKR_OK) break;
         }
         const bool last = (k == nst - 1);
         if (!last) P->stall_cap = stages[k] == PKR_FP16 ? 0.1 : 1e-3;
