@@ -1,12 +1,19 @@
 """Benchmark of the fused stream-and-collide sweep (GLUPS, HBM GB/s).
 
 Workload: 3D periodic 256^3 grid, D3Q111 velocity set with the N=5
-equilibrium, binary64 populations, source = 64 periodic Gaussians (sigma 2
-cells, centres from SplitMix64 seed 0, charges alternating +-1, mean
-removed), tau_lb from Kn = 0.2.  One benchmark step = 32 sweeps followed by
-the binary64 relative-L2 residual check (one pass of the whole hot path: pull,
-density, BGK relaxation, source, store, residual).  The populations (2 x 14.9
-GB) are far larger than L2, so no flush is needed between steps.
+equilibrium, source = 64 periodic Gaussians (sigma 2 cells, centres from
+SplitMix64 seed 0, charges alternating +-1, mean removed), tau_lb from Kn =
+0.2.  Populations are stored as 64-bit fixed point with one power-of-two scale
+per array (PKR_FX64: the density an exact integer sum, the equilibrium and
+source terms in binary64; every stored value resolved to 2^-51 of the
+largest, parity with the binary64 oracle <= 1e-12 at full size), 1784 bytes
+per site update like binary64 storage.  On this GPU the binary64 storage
+sweep is bound by the FP64 pipe (one FMA per velocity and site); its own
+rate and roofline fraction ride on the same line (``other_storage``).  One
+benchmark step = 32 sweeps followed by the binary64 relative-L2 residual
+check (one pass of the whole hot path: pull, density, BGK relaxation, source,
+store, residual).  The populations (2 x 14.9 GB) are far larger than L2, so
+no flush is needed between steps.
 
 ``e2e``: the same metric for a complete solve to rel. residual 1e-10 through
 ``pkr_solve`` with host buffers (H2D of rho and D2H of Phi inside the timed
@@ -46,12 +53,12 @@ sys.path.insert(0, ROOT)
 
 SHAPE = (256, 256, 256)
 LATTICE, ORDER, KN = "D3Q111", 5, 0.2
-PRECISION = "fp64"
+PRECISION = "fx64"   # 64-bit fixed-point storage, binary64-accurate (parity 1e-12)
 TAU = 0.0            # > 0: tau_lb directly instead of the Knudsen number
 SWEEPS_PER_STEP = 32
 SLAB = 16            # planes of the CPU-baseline sample (the reference arm's step too)
 METRIC = "GLUPS (site updates/s, 1e9) of the fused sweep"
-WORKLOAD = "poisson3d_256cube_d3q111_n5_fp64_64gauss_sigma2_seed0_kn0.2"
+WORKLOAD = "poisson3d_256cube_d3q111_n5_fx64_64gauss_sigma2_seed0_kn0.2"
 
 
 def dist_env():
@@ -75,7 +82,7 @@ def configure(args):
     if PRECISION in ("mixed", "mixed_fx64"):
         raise SystemExit("--precision mixed* applies to the batch and serve workloads")
     TAU = args.tau
-    if (SHAPE, LATTICE, ORDER, PRECISION, TAU) != ((256, 256, 256), "D3Q111", 5, "fp64", 0.0):
+    if (SHAPE, LATTICE, ORDER, PRECISION, TAU) != ((256, 256, 256), "D3Q111", 5, "fx64", 0.0):
         n = SHAPE[0]
         WORKLOAD = (f"poisson3d_{n}cube_{LATTICE.lower()}_n{ORDER}_{PRECISION}"
                     f"_64gauss_sigma2_seed0_" + (f"tau{TAU:g}" if TAU > 0 else "kn0.2"))
@@ -139,14 +146,16 @@ def recorded_traffic():
     """DRAM bytes per sweep launch of the headline workload from the committed
     ncu summary, or None if the kernel sources changed since it was taken."""
     import hashlib
-    if (SHAPE, LATTICE, ORDER, PRECISION) != ((256, 256, 256), "D3Q111", 5, "fp64"):
+    if (SHAPE, LATTICE, ORDER) != ((256, 256, 256), "D3Q111", 5) or \
+            PRECISION not in ("fp64", "fx64"):
         return None
     csrc = os.path.join(ROOT, "paper_1504_05869_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("pkr_sweep.cuh", "pkr_lattices.h", "sweep_d3q111.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     try:
-        txt = open(os.path.join(ROOT, "profiles", "sweep_d3q111_fp64_128cube_traffic.md")).read()
+        txt = open(os.path.join(ROOT, "profiles",
+                                f"sweep_d3q111_{PRECISION}_128cube_traffic.md")).read()
     except OSError:
         return None
     vals = dict(line.split(": ", 1) for line in txt.splitlines()
@@ -221,12 +230,13 @@ def cpu_full_solve(pk, torch):
     return out
 
 
-def time_to_1e8(pk, torch, r, phi64, solve64, stream):
+def time_to_1e8(pk, torch, r, stream, e2e_solve, e2e_phi):
     """Time to a solution within ~1e-8 (rel. L2) of the scheme's exact
     binary64 fixed point at 256^3: the FFT comparator gives the fixed point
-    itself; the plain binary64 solve (the e2e solve, host buffers) and the
-    MIXED / MIXED_FX64 ladders (binary32 steps, then binary64 or 64-bit fixed
-    point from the converted state) each run to rel. residual 1e-10."""
+    itself; plain binary64 storage, 64-bit fixed point (the e2e solve, host
+    buffers) and the MIXED / MIXED_FX64 ladders (binary32 steps, then
+    binary64 or 64-bit fixed point from the converted state) each run to rel.
+    residual 1e-10 on device buffers."""
     ref = torch.empty_like(r)
     prob = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN)
     pk.fixed_point_fft(r, ref, prob)                 # warm-up (cuFFT plans)
@@ -236,10 +246,7 @@ def time_to_1e8(pk, torch, r, phi64, solve64, stream):
     torch.cuda.synchronize()
     out = {"fixed_point_fft_s": time.perf_counter() - t0}
     nref = torch.linalg.norm(ref).item()
-    out["fp64"] = {"seconds": solve64["seconds"], "sweeps": solve64["sweeps"],
-                   "status": solve64["status"],
-                   "rel_l2_vs_fixed_point": torch.linalg.norm(phi64 - ref).item() / nref}
-    for prec in ("mixed", "mixed_fx64"):
+    for prec in ("fp64", "mixed", "mixed_fx64"):
         phi = torch.empty_like(r)
         p = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN, tol=1e-10, tol_kind="rel_l2",
                        check_every=SWEEPS_PER_STEP, max_sweeps=200000, precision=prec)
@@ -250,14 +257,50 @@ def time_to_1e8(pk, torch, r, phi64, solve64, stream):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         out[prec] = {"seconds": dt, "sweeps": st["sweeps"], "status": rc,
-                     "rel_l2_vs_fixed_point": torch.linalg.norm(phi - ref).item() / nref,
-                     "speedup_vs_fp64": solve64["seconds"] / dt}
+                     "rel_l2_vs_fixed_point": torch.linalg.norm(phi - ref).item() / nref}
         del phi
+    if PRECISION != "fp64":
+        out[PRECISION] = {"seconds": e2e_solve["seconds"], "sweeps": e2e_solve["sweeps"],
+                          "status": e2e_solve["status"], "host_buffers": True,
+                          "rel_l2_vs_fixed_point":
+                              torch.linalg.norm(e2e_phi - ref).item() / nref}
+    t64 = out["fp64"]["seconds"]
+    for k in list(out):
+        if isinstance(out[k], dict) and k != "fp64":
+            out[k]["speedup_vs_fp64"] = t64 / out[k]["seconds"]
     del ref
     torch.cuda.empty_cache()
-    out["note"] = ("each run to rel. residual 1e-10; the fp64 time is the e2e solve "
-                   "(host buffers, copies included)")
+    out["note"] = ("each run to rel. residual 1e-10 (device buffers; the "
+                   f"{PRECISION} entry is the e2e solve, host copies included)")
     return out
+
+
+def sweep_rate(pk, torch, r, precision, steps, stream, hbm_peak):
+    """Autotuned sweep throughput of another storage mode on the same input
+    (reported beside the headline): GLUPS, HBM GB/s and fraction of peak."""
+    prob = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN, tol=0.0, check_every=SWEEPS_PER_STEP,
+                      max_sweeps=10 ** 9, precision=precision)
+    with torch.cuda.stream(stream):
+        plan = pk.Plan(prob, stream=stream)
+        plan.load_source(r)
+    variant, _ = plan.autotune(2)
+    plan.run(SWEEPS_PER_STEP)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.run(SWEEPS_PER_STEP)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.close()
+    launch_ms = e0.elapsed_time(e1) / (steps * SWEEPS_PER_STEP)
+    V = r.numel()
+    es = {"fp64": 8, "fx64": 8, "fp32": 4, "fp16": 2}[precision]
+    bs = 2 * 111 * es + (8 if precision in ("fp64", "fx64") else 4)
+    gbs = V * bs / (launch_ms * 1e-3) / 1e9
+    return {"glups": V / (launch_ms * 1e-3) / 1e9, "hbm_gbs": gbs, "frac": gbs / hbm_peak,
+            "ms_per_sweep": launch_ms, "bytes_per_site": bs, "kernel_variant": variant,
+            "steps": steps, "sweeps_per_step": SWEEPS_PER_STEP}
 
 
 def run_reference(args):
@@ -310,7 +353,8 @@ def run(args):
     V = rho.size
     stream = torch.cuda.Stream()
     prob = pk.problem(LATTICE, SHAPE, ORDER, knudsen=KN, tau_lb=TAU, tol=0.0,
-                      check_every=SWEEPS_PER_STEP, max_sweeps=10 ** 9, precision=PRECISION)
+                      check_every=SWEEPS_PER_STEP, max_sweeps=10 ** 9, precision=PRECISION,
+                      variant=args.variant)
     # tau_lb = 1 in binary64 runs the scalar stencil (Phi-only state)
     stencil = TAU == 1.0 and PRECISION == "fp64"
     r_dev = torch.from_numpy(rho).cuda()
@@ -325,7 +369,10 @@ def run(args):
         rc, st = plan.run(SWEEPS_PER_STEP)
         return st
 
-    variant, tuned_ms = plan.autotune(2)
+    if args.variant >= 0:        # a fixed geometry (profiling); default: autotuned
+        variant = args.variant
+    else:
+        variant, tuned_ms = plan.autotune(2)
     for _ in range(args.warmup):
         st = step()
     tau = st["tau_lb"]
@@ -392,11 +439,12 @@ def run(args):
                          "status": rc, "seconds": e_s, "tol": 1e-10}}
 
     # the reference's other two metrics, on one GPU, after the timed region
-    t2e8 = serving = None
-    if world == 1 and not args.no_extras and e2e is not None and PRECISION == "fp64" \
-            and TAU == 0.0:
-        t2e8 = time_to_1e8(pk, torch, r_dev, phi_h.cuda(),
-                           e2e["solve"], stream)
+    t2e8 = serving = other = None
+    if world == 1 and not args.no_extras and e2e is not None and TAU == 0.0 and \
+            PRECISION in ("fp64", "fx64") and (LATTICE, ORDER, SHAPE) == ("D3Q111", 5, (256,) * 3):
+        other_prec = "fp64" if PRECISION == "fx64" else "fx64"
+        other = {other_prec: sweep_rate(pk, torch, r_dev, other_prec, 4, stream, hbm_peak)}
+        t2e8 = time_to_1e8(pk, torch, r_dev, stream, e2e["solve"], phi_h.cuda())
         serving = {"overloaded": serve_trace(pk, args.serve_requests, 200.0, "mixed", 150.0),
                    "sub_capacity": serve_trace(pk, args.serve_sub_requests,
                                                args.serve_sub_rate, "mixed", 150.0)}
@@ -419,7 +467,9 @@ def run(args):
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                     "unit": "GB/s", "frac": achieved / hbm_peak,
                     "traffic": recorded_traffic(), "peak_source": peak_src,
-                    "kernel": f"sweep_staged_kernel<{LATTICE},"
+                    "kernel": ("sweep_ws_kernel" if variant >= pk._pkr.pkr_batch_variant_count(
+                                   pk.LATTICES[LATTICE]) else "sweep_staged_kernel") +
+                              f"<{LATTICE},"
                               f"{ {'fp64': 'double', 'fx64': 'long long'}.get(PRECISION, 'float') }>",
                     "algorithmic_bytes_per_launch": V * bytes_site}
     if rank == 0:
@@ -440,7 +490,7 @@ def run(args):
             "hbm_gbs": V * bytes_site * sweeps * world / (dev_ms * 1e-3) / 1e9,
             "roofline": roofline,
             "cpu_baseline": cpu, "cpu_baseline_openmp": cpu_omp, "cpu_full_solve": cpu_full,
-            "e2e": e2e, "time_to_1e8": t2e8, "serving": serving,
+            "other_storage": other, "e2e": e2e, "time_to_1e8": t2e8, "serving": serving,
             "clocks": clocks, "gpu_launches": args.steps * (SWEEPS_PER_STEP + 1),
             "wall_s": wall,
         }
@@ -967,6 +1017,38 @@ def run_tau1(args):
     return 0
 
 
+def run_pull_ceiling(args):
+    """Memory ceiling of the sweep's access pattern at 256^3 (pkr_pull_copy_
+    ceiling): the bytes of one D3Q111 sweep moved with no arithmetic, through
+    the sweep's own staging, with the pull offsets kept per axis, for 8- and
+    4-byte populations; beside D3Q19's."""
+    import ctypes
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1504_05869_gb300 as pk
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+    n = (ctypes.c_int64 * 3)(*SHAPE)
+    out = {}
+    for lattice in ("D3Q111", "D3Q19"):
+        for elem in (8, 4):
+            for axes, label in ((0, "none"), (2, "yz"), (1, "x"), (3, "xyz")):
+                g = ctypes.c_double()
+                rc = pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES[lattice], n, elem, axes, 5,
+                                                   ctypes.byref(g), None)
+                out[f"{lattice}_{elem}B_shift_{label}"] = (
+                    {"gbs": g.value, "frac_of_copy_peak": g.value / peak} if rc == 0
+                    else {"status": rc})
+    torch.cuda.synchronize()
+    line = {"metric": "GB/s of the sweep's access pattern without arithmetic",
+            "workload": "pull-ceiling", "value": out["D3Q111_8B_shift_xyz"].get("gbs"),
+            "unit": "GB/s", "copy_peak_gbs": peak, "runs": out,
+            "config": {"grid": list(SHAPE), "staging": "per-lane cp.async, 32-site tiles, "
+                       "2 velocity groups x 2 tiles per block"}, "data": "synthetic (zeros)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -984,13 +1066,13 @@ def main():
     ap.add_argument("--size", type=int, default=0, help="cube edge (default 256)")
     ap.add_argument("--lattice", default="D3Q111", choices=["D3Q111", "D3Q19"])
     ap.add_argument("--order", type=int, default=5)
-    ap.add_argument("--precision", default="fp64",
+    ap.add_argument("--precision", default="fx64",
                     choices=["fp64", "fp32", "fp16", "fx64", "mixed", "mixed_fx64"],
                     help="sweep workload: fp64/fp32/fp16/fx64; batch/serve: "
                          "fp64/fp32/fx64/mixed/mixed_fx64")
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "batch", "serve", "poisson2d", "precision", "tau1",
-                             "knudsen", "paper1d"])
+                             "knudsen", "paper1d", "pull-ceiling"])
     ap.add_argument("--no-512", action="store_true")
     ap.add_argument("--solve-512", action="store_true",
                     help="precision workload: also solve at 512^3 against the FFT fixed point")
@@ -1000,6 +1082,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--tol", type=float, default=0.0)
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="sweep workload: a fixed kernel geometry instead of the autotuned one")
     ap.add_argument("--tau1-budget-s", type=float, default=90.0,
                     help="knudsen workload: GPU seconds per lattice for the tau_lb = 1 runs")
     ap.add_argument("--skip-kn", action="store_true",
@@ -1021,6 +1105,8 @@ def main():
         return run_knudsen(args)
     if args.workload == "paper1d":
         return run_paper1d(args)
+    if args.workload == "pull-ceiling":
+        return run_pull_ceiling(args)
     configure(args)
     if args.impl == "reference":
         return run_reference(args)

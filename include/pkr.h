@@ -390,6 +390,28 @@ int pkr_ctx_info(pkr_ctx *ctx, int64_t *finished, double *site_updates, int64_t 
 int pkr_ctx_destroy(pkr_ctx *ctx);
 
 /* ---------------------------------------------------------------------
+ * Memory ceiling of the sweep's access pattern (a diagnostic for the
+ * roofline; the paper has no counterpart).
+ *
+ * Moves the bytes of one sweep without arithmetic: Q planes of V values of
+ * elem_bytes (8: binary64 or fixed point, 4: binary32) read through the
+ * sweep's per-lane asynchronous copies of 32-site tiles into shared memory
+ * and written back with streaming stores, in the staged sweep's default
+ * geometry (2 velocity groups x 2 tiles per block of 4 warps), as many
+ * blocks as fit.  shift_axes selects which components of the pull offsets -v_i are
+ * kept: 0 none (a plain copy of Q planes), 1 x only, 2 y and z only, 3 all
+ * (the sweep's pull).  Runs one untimed and `reps` timed copies on `stream`
+ * and returns, in *gbs, the bytes read and written per second (1e9 B/s).
+ * It allocates 2 x Q x V x elem_bytes of device memory for the call.
+ * lattice: PKR_D3Q19 or PKR_D3Q111; every edge at least the lattice's reach.
+ * Errors: PKR_EINVAL (other lattices or element sizes, an edge below the
+ * reach, V outside [1, 2^31 - 1], reps < 1, shift_axes outside 0..3),
+ * PKR_ENOMEM, PKR_ECUDA.
+ */
+int pkr_pull_copy_ceiling(int lattice, const int64_t n[3], int elem_bytes, int shift_axes,
+                          int reps, double *gbs, void *stream);
+
+/* ---------------------------------------------------------------------
  * Allocation-free residual (the paper has no counterpart: this is a service
  * for callers that cannot allocate device memory -- runtimes whose device
  * memory all belongs to their own pool and that forbid side allocations, and

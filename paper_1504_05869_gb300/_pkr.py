@@ -34,7 +34,7 @@ EXPORTS = [
     "pkr_batch_variant_count",
     "pkr_plan_autotune", "pkr_ctx_create", "pkr_submit", "pkr_poll", "pkr_ctx_run",
     "pkr_ctx_wait", "pkr_ctx_info", "pkr_ctx_destroy", "pkr_plan_import",
-    "pkr_fixed_point_fft", "pkr_ctx_release",
+    "pkr_fixed_point_fft", "pkr_ctx_release", "pkr_pull_copy_ceiling",
 ]
 
 
@@ -96,6 +96,8 @@ _SIGS = {
                                            ctypes.POINTER(pkr_stats), _P]),
     "pkr_variant_count": (ctypes.c_int, [ctypes.c_int]),
     "pkr_batch_variant_count": (ctypes.c_int, [ctypes.c_int]),
+    "pkr_pull_copy_ceiling": (ctypes.c_int, [ctypes.c_int, _I64, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, _D, _P]),
     "pkr_plan_autotune": (ctypes.c_int, [_P, ctypes.c_int, _I32, _D]),
     "pkr_ctx_create": (ctypes.c_int, [ctypes.POINTER(pkr_ctx_config), _P, ctypes.POINTER(_P)]),
     "pkr_submit": (ctypes.c_int, [_P, ctypes.POINTER(pkr_problem), _P, _P, ctypes.c_int,
@@ -167,6 +169,7 @@ pkr_residual_noalloc = _fn("pkr_residual_noalloc")
 pkr_fixed_point_fft = _fn("pkr_fixed_point_fft")
 pkr_variant_count = _fn("pkr_variant_count")
 pkr_batch_variant_count = _fn("pkr_batch_variant_count")
+pkr_pull_copy_ceiling = _fn("pkr_pull_copy_ceiling")
 pkr_plan_autotune = _fn("pkr_plan_autotune")
 pkr_ctx_create = _fn("pkr_ctx_create")
 pkr_submit = _fn("pkr_submit")

@@ -592,3 +592,24 @@ def test_ladder_hands_over_at_the_rounding_floor(pk, monkeypatch, precision):
     assert rc == 0 and rc64 == 0 and st["residual"] < 1e-12
     assert st["sweeps"] < 3 * st64["sweeps"]
     assert _rel(got, star) < 5e-9 and _rel(g64, star) < 5e-9
+
+
+def test_pull_copy_ceiling_diagnostic(pk):
+    """The access-pattern diagnostic moves the sweep's bytes without
+    arithmetic: every offset mode runs, and keeping the x offsets (warp
+    accesses that straddle cache lines) is never faster than dropping them."""
+    import ctypes
+    n = (ctypes.c_int64 * 3)(64, 64, 64)
+    got = {}
+    for axes in (0, 1, 2, 3):
+        g = ctypes.c_double()
+        assert pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES["D3Q111"], n, 8, axes, 3,
+                                             ctypes.byref(g), None) == 0
+        assert g.value > 100.0
+        got[axes] = g.value
+    assert got[3] <= 1.1 * got[2]
+    g = ctypes.c_double()
+    assert pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES["D2Q169"], n, 8, 3, 3, ctypes.byref(g),
+                                         None) == pk._pkr.PKR_EINVAL
+    assert pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES["D3Q111"], n, 2, 3, 3, ctypes.byref(g),
+                                         None) == pk._pkr.PKR_EINVAL
