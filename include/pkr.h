@@ -79,6 +79,10 @@ typedef enum pkr_lattice {
  * FP16: populations stored in binary16 with a power-of-two scale per array
  * (set before each step so that the step's largest value has 4x headroom),
  * arithmetic in binary32, source in binary32; accurate to ~1e-4 of Phi.
+ * Where nx is a multiple of 64 and no edge is below the lattice's reach, the
+ * sweep gives each lane two adjacent sites (variant 1, the default there;
+ * variant 0 keeps one site per lane); both give the same Phi bit for bit
+ * between residual checks.
  * MIXED16 (pkr_solve only): binary16 to PKR_MIXED16_SWITCH_TOL, binary32 to
  * PKR_MIXED_SWITCH_TOL, then binary64 to tol.
  * A reduced-precision rung also hands over at its rounding floor, which can

@@ -19,8 +19,8 @@ namespace pkr {
 template <class L, typename T> int launch_sweep_t(int, const SweepArgs&, const void*, int, void*);
 template <class L, typename T> int occupancy_t(int, int*, int*);
 template <class L> int variant_count_t();
-template <class L> int launch_sweep_h16(const SweepArgs&, const void*, int, void*);
-template <class L> int occupancy_h16(int*, int*);
+template <class L> int launch_sweep_h16(int, const SweepArgs&, const void*, int, void*);
+template <class L> int occupancy_h16(int, int*, int*);
 template <class L>
 int launch_stencil(const double*, double*, const double*, const Coefs<double>&, int64_t, int, int,
                    int, int, int, double*, int, void*, const int*);
@@ -50,6 +50,16 @@ int dispatch_occ(int var, int prec, int* b, int* tpb)
 }
 
 int64_t tiles_of(const int64_t n[3]) { return (n[0] * n[1] * n[2] + 31) / 32; }
+
+// The two-sites-per-lane binary16 sweep applies: x rows of whole 64-site
+// tiles, every edge at least the lattice's reach.
+bool h16_pairs(const pkr_problem* p, const LatticeInfo& li)
+{
+    if (p->n[0] % 64 != 0) return false;
+    for (int k = 0; k < li.dim; ++k)
+        if (p->n[k] < li.reach) return false;
+    return true;
+}
 
 int variant_count(int lattice)
 {
@@ -139,6 +149,7 @@ struct pkr_plan {
     // (pkr_plan_run returns PKR_OK) once the residual, below this cap, stops
     // falling from one check to the next (the storage's rounding floor)
     double stall_cap;
+    bool h16pairs;      // binary16 storage: the two-sites-per-lane sweep applies
     cudaStream_t stream;
     int device, grid, red_blocks, elem, small, variant, nsm;
     int64_t ntiles;
@@ -259,15 +270,16 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
     a.oflow = P->h16of;
     a.stop = P->stop_arg;
     if (pr == PKR_FP16) {
+        const int vh = (vr == 1 && P->h16pairs) ? 1 : 0;
         switch (P->prob.lattice) {
-        case PKR_D1Q5: rc = launch_sweep_h16<D1Q5>(a, c, P->grid, P->stream); break;
-        case PKR_D1Q9: rc = launch_sweep_h16<D1Q9>(a, c, P->grid, P->stream); break;
-        case PKR_D1Q13: rc = launch_sweep_h16<D1Q13>(a, c, P->grid, P->stream); break;
-        case PKR_D2Q25: rc = launch_sweep_h16<D2Q25>(a, c, P->grid, P->stream); break;
-        case PKR_D2Q81: rc = launch_sweep_h16<D2Q81>(a, c, P->grid, P->stream); break;
-        case PKR_D2Q169: rc = launch_sweep_h16<D2Q169>(a, c, P->grid, P->stream); break;
-        case PKR_D3Q19: rc = launch_sweep_h16<D3Q19>(a, c, P->grid, P->stream); break;
-        case PKR_D3Q111: rc = launch_sweep_h16<D3Q111>(a, c, P->grid, P->stream); break;
+        case PKR_D1Q5: rc = launch_sweep_h16<D1Q5>(vh, a, c, P->grid, P->stream); break;
+        case PKR_D1Q9: rc = launch_sweep_h16<D1Q9>(vh, a, c, P->grid, P->stream); break;
+        case PKR_D1Q13: rc = launch_sweep_h16<D1Q13>(vh, a, c, P->grid, P->stream); break;
+        case PKR_D2Q25: rc = launch_sweep_h16<D2Q25>(vh, a, c, P->grid, P->stream); break;
+        case PKR_D2Q81: rc = launch_sweep_h16<D2Q81>(vh, a, c, P->grid, P->stream); break;
+        case PKR_D2Q169: rc = launch_sweep_h16<D2Q169>(vh, a, c, P->grid, P->stream); break;
+        case PKR_D3Q19: rc = launch_sweep_h16<D3Q19>(vh, a, c, P->grid, P->stream); break;
+        case PKR_D3Q111: rc = launch_sweep_h16<D3Q111>(vh, a, c, P->grid, P->stream); break;
         default: return PKR_EINVAL;
         }
         if (rc != 0) return PKR_ECUDA;
@@ -307,14 +319,14 @@ int occupancy(int variant, int lattice, int precision, int* b, int* tpb)
 {
     if (precision == PKR_FP16) {
         switch (lattice) {
-        case PKR_D1Q5: return occupancy_h16<D1Q5>(b, tpb);
-        case PKR_D1Q9: return occupancy_h16<D1Q9>(b, tpb);
-        case PKR_D1Q13: return occupancy_h16<D1Q13>(b, tpb);
-        case PKR_D2Q25: return occupancy_h16<D2Q25>(b, tpb);
-        case PKR_D2Q81: return occupancy_h16<D2Q81>(b, tpb);
-        case PKR_D2Q169: return occupancy_h16<D2Q169>(b, tpb);
-        case PKR_D3Q19: return occupancy_h16<D3Q19>(b, tpb);
-        case PKR_D3Q111: return occupancy_h16<D3Q111>(b, tpb);
+        case PKR_D1Q5: return occupancy_h16<D1Q5>(variant, b, tpb);
+        case PKR_D1Q9: return occupancy_h16<D1Q9>(variant, b, tpb);
+        case PKR_D1Q13: return occupancy_h16<D1Q13>(variant, b, tpb);
+        case PKR_D2Q25: return occupancy_h16<D2Q25>(variant, b, tpb);
+        case PKR_D2Q81: return occupancy_h16<D2Q81>(variant, b, tpb);
+        case PKR_D2Q169: return occupancy_h16<D2Q169>(variant, b, tpb);
+        case PKR_D3Q19: return occupancy_h16<D3Q19>(variant, b, tpb);
+        case PKR_D3Q111: return occupancy_h16<D3Q111>(variant, b, tpb);
         }
         return -1;
     }
@@ -556,7 +568,11 @@ int plan_create(const pkr_problem* p, void* stream, pkr_plan** out, bool spare)
     P->ntiles = tiles_of(p->n);
     const int nvar = variant_count(p->lattice);
     int var = (p->variant >= 0) ? p->variant : default_variant(p->lattice, p->precision, P->V, nsm);
-    if (p->precision == PKR_FP16) var = 0;   // one geometry for binary16 storage
+    // binary16 storage: two sites per lane where every x row splits into
+    // 64-site tiles (and no edge is below the reach), unless variant 0 (one
+    // site per lane) is asked for; else one
+    P->h16pairs = p->precision == PKR_FP16 && h16_pairs(p, li);
+    if (p->precision == PKR_FP16) var = (P->h16pairs && p->variant != 0) ? 1 : 0;
     if (var >= nvar) {
         delete P;
         return PKR_EINVAL;
@@ -785,7 +801,9 @@ int pkr_plan_autotune(pkr_plan* P, int steps_per_variant, int32_t* best_variant,
                       double* best_ms_per_step)
 {
     if (!P || !P->loaded || steps_per_variant < 1) return PKR_EINVAL;
-    const int n = P->stencil ? 1 : variant_count(P->prob.lattice);
+    const int n = P->stencil ? 1
+                  : P->prob.precision == PKR_FP16 ? (P->h16pairs ? 2 : 1)
+                                                   : variant_count(P->prob.lattice);
     cudaEvent_t e0, e1;
     PKR_CK(cudaEventCreate(&e0));
     PKR_CK(cudaEventCreate(&e1));

@@ -1074,27 +1074,269 @@ sweep_h16_kernel(const SweepArgs a, const Coefs<float> c)
     }
 }
 
-template <class L>
-int launch_sweep_h16(const SweepArgs& a, const void* coefs, int grid, void* stream)
+// ---------------------------------------------------------------------------
+// binary16 storage, two sites per lane.  A warp owns a tile of 64 consecutive
+// sites of one x row (nx a multiple of 64, every edge at least the lattice's
+// reach) and lane l the pair of sites x0 + 2l, x0 + 2l + 1: one aligned
+// 4-byte word of every plane.  For velocity i the pulled elements start at
+// x0 - v_x, whose parity is that of v_x, known at compile time: an even start
+// is 32 aligned words (lane l's pair is word l), an odd one 33 (lane l's pair
+// is the high half of word l and the low half of word l + 1).  Each lane
+// copies word l of the run (lane 0 also word 32 of an odd run) into the
+// velocity's 33-word slot.  After the copies each odd run is repacked in
+// place into aligned pairs, and both passes read one word per velocity and
+// lane, converted where it is used.  Per site, the density, relaxation, scaling,
+// overflow bound and rounding are those of sweep_h16_kernel, operation for
+// operation, so the two give the same results bit for bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int prmt(unsigned int a, unsigned int b, unsigned int sel)
 {
-    constexpr int TILES = 2;
-    const size_t smem = (size_t)TILES * L::Q * 32 * 4;
-    sweep_h16_kernel<L, TILES><<<grid, TILES * 32, smem, (cudaStream_t)stream>>>(
-        a, *static_cast<const Coefs<float>*>(coefs));
+    unsigned int r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+    return r;
+}
+
+// Lane's pair of a velocity from its slot (sw: this lane's word, 4 l), after
+// the repack: one aligned word, low half the even site, high half the odd one.
+__device__ __forceinline__ float2 h16_word(uint32_t sw)
+{
+    const unsigned int w = lds_b32(sw);
+    return __half22float2(*reinterpret_cast<const __half2*>(&w));
+}
+
+template <class L, int TILES>
+__global__ void __launch_bounds__(TILES * 32, 7)   // 128 registers: 7 blocks per SM
+sweep_h16p_kernel(const SweepArgs a, const Coefs<float> c)
+{
+    constexpr int Q = L::Q;
+    constexpr int RC = reach_of<L>();
+    constexpr int W = 2 * RC + 1;
+    constexpr int NC = ncls_of<L>();
+    constexpr int SW = 33 * 4;                 // bytes of one velocity's slot
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double rpart[TILES][4];
+    __shared__ float mpart[TILES];
+
+    const int lane = threadIdx.x & 31;
+    const int sub = threadIdx.x >> 5;
+    const uint32_t slot = (uint32_t)__cvta_generic_to_shared(smem_raw) + (uint32_t)(sub * Q * SW);
+    const uint32_t sw = slot + (uint32_t)(lane * 4);
+    // one scratch word per lane past the slots of the block's tiles
+    const uint32_t dummy = (uint32_t)__cvta_generic_to_shared(smem_raw) +
+                           (uint32_t)(TILES * Q * SW + threadIdx.x * 4);
+    const unsigned int* __restrict__ A = static_cast<const unsigned int*>(a.A);   // words
+    unsigned int* __restrict__ B = static_cast<unsigned int*>(a.B);
+    const float* __restrict__ S = static_cast<const float*>(a.S);
+    const int64_t V = a.V;
+    const int64_t Vw = V >> 1;                 // words per plane (V is even)
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int nw = nx >> 1;                    // words per row
+    const float sr = a.sc[a.cur];
+    const float inv_sw = 1.0f / a.sc[a.cur ^ 1];
+    const int ntiles = (int)(V >> 6);
+
+    double rd2 = 0.0, rn2 = 0.0, rmx = 0.0, rms = 0.0;
+    float pmax = 0.f;
+    const int nt = gridDim.x * TILES;
+    for (int tile = blockIdx.x * TILES + sub; tile < ntiles; tile += nt) {
+        const int s0 = tile * 64;              // first site: x0 = s0 mod nx, even
+        const int r = (int)((unsigned)s0 / (unsigned)nx);
+        const int x0 = s0 - r * nx;
+        const int z = (int)((unsigned)r / (unsigned)ny);
+        const int y = r - z * ny;
+        int yo[W], zo[W];
+        static_for<0, W>([&](auto DI) {
+            constexpr int d = decltype(DI)::value - RC;
+            yo[d + RC] = wrap_off<d>(y, ny) * nw;
+            zo[d + RC] = wrap_off<d>(z, nz) * (ny * nw);
+        });
+        const int nb = a.zero_in ? 0 : 4;
+        // lane's word of the run for each x displacement -R..R (the first
+        // word of a run is (x0 - vx) rounded down to even, halved)
+        int wl[W];
+        static_for<0, W>([&](auto DI) {
+            constexpr int vx = decltype(DI)::value - RC;
+            int w = ((x0 - vx) >> 1) + lane;   // arithmetic shift: floor
+            wl[vx + RC] = w < 0 ? w + nw : (w >= nw ? w - nw : w);
+        });
+        const unsigned int* plane = A;          // plane i, advanced per velocity
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int vx = vx_of<L>(i);
+            constexpr int oy = vy_of<L>(i) + RC;
+            constexpr int oz = vz_of<L>(i) + RC;
+            const unsigned int* row = plane + (zo[oz] + yo[oy]);
+            plane += Vw;
+            cp_async<4>(sw + (uint32_t)(i * SW), row + wl[vx + RC], nb);
+            if constexpr (vx & 1) {
+                // word 32 of an odd run, copied by lane 0; the other lanes
+                // issue the same instruction with nothing to read, into a
+                // word of their own (no branch in the unrolled pull)
+                int w1 = ((x0 - vx) >> 1) + 32;
+                w1 = w1 >= nw ? w1 - nw : w1;
+                cp_async<4>(lane == 0 ? slot + (uint32_t)(i * SW + 128) : dummy, row + w1,
+                            lane == 0 ? nb : 0);
+            }
+        });
+        cp_async_wait_all();
+        __syncwarp();
+        // repack every odd run in place into aligned pairs: word l := high
+        // half of word l, low half of word l + 1 (all lanes read before any
+        // writes), so both passes below read one aligned word per velocity
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            if constexpr (vx_of<L>(i) & 1) {
+                const uint32_t ad = sw + (uint32_t)(i * SW);
+                const unsigned int w = prmt(lds_b32(ad), lds_b32(ad + 4), 0x5432);
+                __syncwarp();
+                asm volatile("st.shared.b32 [%0], %1;" ::"r"(ad), "r"(w) : "memory");
+            }
+        });
+        __syncwarp();
+
+        // density: per site the four interleaved binary32 partials of
+        // density_fixed_f32 (velocity k to partial k mod 4, the last Q mod 4
+        // to partial 0), then the array's scale
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+#pragma unroll 2
+        for (int k = 0; k + 3 < Q; k += 4) {
+            const float2 v0 = h16_word(sw + (uint32_t)((k + 0) * SW));
+            const float2 v1 = h16_word(sw + (uint32_t)((k + 1) * SW));
+            const float2 v2 = h16_word(sw + (uint32_t)((k + 2) * SW));
+            const float2 v3 = h16_word(sw + (uint32_t)((k + 3) * SW));
+            a0 += v0.x; b0 += v0.y;
+            a1 += v1.x; b1 += v1.y;
+            a2 += v2.x; b2 += v2.y;
+            a3 += v3.x; b3 += v3.y;
+        }
+#pragma unroll
+        for (int k = Q - Q % 4; k < Q; ++k) {
+            const float2 v = h16_word(sw + (uint32_t)(k * SW));
+            a0 += v.x; b0 += v.y;
+        }
+        const float PhiA = ((a0 + a1) + (a2 + a3)) * sr;
+        const float PhiB = ((b0 + b1) + (b2 + b3)) * sr;
+        // the written array's scale inv_sw is a power of two, so it enters the
+        // relaxation factor and the per-class terms exactly: the products
+        // below are the stored values p / sc, bit for bit those of p * inv_sw
+        const float om1w = c.om1 * sr * inv_sw;
+        const int s = s0 + 2 * lane;
+        const float2 S2 = *reinterpret_cast<const float2*>(S + s);
+        const float SxA = (float)((double)S2.x + a.soff);
+        const float SxB = (float)((double)S2.y + a.soff);
+        unsigned int* dst = B + (s >> 1);       // plane i's word of the pair, per velocity
+        static_for<0, NC>([&](auto CI) {
+            constexpr int cl = decltype(CI)::value;
+            constexpr int i0 = cls_begin<L>(cl), i1 = cls_begin<L>(cl + 1);
+            const float eA = fmaf(c.wphi[cl], PhiA, c.chi[cl] * SxA) * inv_sw;
+            const float eB = fmaf(c.wphi[cl], PhiB, c.chi[cl] * SxB) * inv_sw;
+#pragma unroll 4
+            for (int i = i0; i < i1; ++i) {
+                const float2 v = h16_word(sw + (uint32_t)(i * SW));
+                const float qA = fmaf(om1w, v.x, eA);   // p / sc of the written array
+                const float qB = fmaf(om1w, v.y, eB);
+                pmax = fmaxf(pmax, fmaxf(fabsf(qA), fabsf(qB)));
+                const __half2 h = __floats2half2_rn(qA, qB);
+                __stcs(dst, *reinterpret_cast<const unsigned int*>(&h));
+                dst += Vw;
+            }
+        });
+        if (a.mode != kPlain) {
+            const double phA = (double)PhiA, phB = (double)PhiB;
+            if (a.mode == kCheck) {
+                const double2 old = *reinterpret_cast<const double2*>(a.Phi + s);
+                const double dA = phA - old.x, dB = phB - old.y;
+                rd2 += dA * dA;
+                rd2 += dB * dB;
+                rn2 += phA * phA;
+                rn2 += phB * phB;
+                rmx = fmax(rmx, fmax(fabs(dA), fabs(dB)));
+                rms += phA;
+                rms += phB;
+            }
+            *reinterpret_cast<double2*>(a.Phi + s) = make_double2(phA, phB);
+        }
+        __syncwarp();
+    }
+
+    // pmax holds max |p| / sc (the stored magnitudes): back to max |p|, exactly
+    pmax = pmax / inv_sw;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_down_sync(0xffffffffu, pmax, o));
+    if (lane == 0) mpart[sub] = pmax;
+    if (a.mode == kCheck) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rd2 += __shfl_down_sync(0xffffffffu, rd2, o);
+            rn2 += __shfl_down_sync(0xffffffffu, rn2, o);
+            rmx = fmax(rmx, __shfl_down_sync(0xffffffffu, rmx, o));
+            rms += __shfl_down_sync(0xffffffffu, rms, o);
+        }
+        if (lane == 0) {
+            rpart[sub][0] = rd2;
+            rpart[sub][1] = rn2;
+            rpart[sub][2] = rmx;
+            rpart[sub][3] = rms;
+        }
+    }
+    // a stored value beyond the binary16 range (it became +-inf) overflowed
+    const int of = !(pmax * inv_sw <= 65504.f);
+    if (__any_sync(0xffffffffu, of) && lane == 0) atomicOr(a.oflow, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int k = 0; k < TILES; ++k) m = fmaxf(m, mpart[k]);
+        atomicMax(a.pmax, __float_as_uint(m));
+        if (a.mode == kCheck) {
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+            for (int k = 0; k < TILES; ++k) {
+                t0 += rpart[k][0];
+                t1 += rpart[k][1];
+                t2 = fmax(t2, rpart[k][2]);
+                t3 += rpart[k][3];
+            }
+            a.partials[4 * blockIdx.x + 0] = t0;
+            a.partials[4 * blockIdx.x + 1] = t1;
+            a.partials[4 * blockIdx.x + 2] = t2;
+            a.partials[4 * blockIdx.x + 3] = t3;
+        }
+    }
+}
+
+// binary16 geometries: 0 one site per lane (any grid), 1 two sites per lane
+// (nx a multiple of 64 and no edge below the reach; the plan checks).
+constexpr int kH16Tiles = 2;
+template <class L>
+constexpr size_t h16_smem(int variant)
+{
+    return variant == 1 ? (size_t)kH16Tiles * (L::Q * 33 * 4 + 32 * 4)
+                        : (size_t)kH16Tiles * L::Q * 32 * 4;
+}
+
+template <class L>
+int launch_sweep_h16(int variant, const SweepArgs& a, const void* coefs, int grid, void* stream)
+{
+    const Coefs<float>& c = *static_cast<const Coefs<float>*>(coefs);
+    if (variant == 1)
+        sweep_h16p_kernel<L, kH16Tiles><<<grid, kH16Tiles * 32, h16_smem<L>(1),
+                                         (cudaStream_t)stream>>>(a, c);
+    else
+        sweep_h16_kernel<L, kH16Tiles><<<grid, kH16Tiles * 32, h16_smem<L>(0),
+                                        (cudaStream_t)stream>>>(a, c);
     return (int)cudaGetLastError();
 }
 
 template <class L>
-int occupancy_h16(int* blocks, int* tiles_per_block)
+int occupancy_h16(int variant, int* blocks, int* tiles_per_block)
 {
-    constexpr int TILES = 2;
-    const size_t smem = (size_t)TILES * L::Q * 32 * 4;
-    auto kern = sweep_h16_kernel<L, TILES>;
+    const size_t smem = h16_smem<L>(variant);
+    auto kern = variant == 1 ? sweep_h16p_kernel<L, kH16Tiles> : sweep_h16_kernel<L, kH16Tiles>;
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    *tiles_per_block = TILES;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, TILES * 32, smem);
+    // tiles_per_block counts 32-site tiles: a two-site tile is two of them
+    *tiles_per_block = variant == 1 ? 2 * kH16Tiles : kH16Tiles;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kH16Tiles * 32, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -1279,8 +1521,8 @@ int batch_variant_count_t() { return Variants<L>::N; }
     template int occupancy_t<L, float>(int, int*, int*);                                     \
     template int variant_count_t<L>();                                                      \
     template int batch_variant_count_t<L>();                                                \
-    template int launch_sweep_h16<L>(const SweepArgs&, const void*, int, void*);             \
-    template int occupancy_h16<L>(int*, int*);                                               \
+    template int launch_sweep_h16<L>(int, const SweepArgs&, const void*, int, void*);        \
+    template int occupancy_h16<L>(int, int*, int*);                                          \
     template int launch_stencil<L>(const double*, double*, const double*, const Coefs<double>&,  \
                                    int64_t, int, int, int, int, int, double*, int, void*,       \
                                    const int*);                                                 \

@@ -613,3 +613,32 @@ def test_pull_copy_ceiling_diagnostic(pk):
                                          None) == pk._pkr.PKR_EINVAL
     assert pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES["D3Q111"], n, 2, 3, 3, ctypes.byref(g),
                                          None) == pk._pkr.PKR_EINVAL
+
+
+@pytest.mark.parametrize("lattice,order,shape,tau", [
+    ("D3Q111", 5, (8, 6, 64), 1.3), ("D3Q111", 5, (5, 4, 128), 0.8),
+    ("D3Q19", 1, (4, 7, 64), 0.9), ("D2Q81", 5, (9, 128), 1.2), ("D1Q13", 7, (192,), 1.1),
+])
+def test_fp16_two_sites_per_lane(pk, lattice, order, shape, tau):
+    """binary16 storage on grids whose x rows split into 64-site tiles runs the
+    two-sites-per-lane sweep.  Between residual checks it gives the one-site
+    sweep's Phi bit for bit (the same operations per site); with checks every
+    4 steps the mass corrections (sums over the grid in a different order)
+    may move the last bits; both match the oracle within the binary16 bound."""
+    import torch
+    rho = _rand(shape, 44)
+    steps = 9
+    ref = oracle.solve(rho, lattice, order, tau_lb=tau, max_steps=steps).phi
+    out = {}
+    for var in (0, -1):
+        for every in (1000, 4):
+            prob = pk.problem(lattice, rho.shape, order, tau_lb=tau, max_sweeps=steps,
+                              check_every=every, precision="fp16", variant=var)
+            r = torch.from_numpy(rho).cuda()
+            phi = torch.empty_like(r)
+            rc, st = pk.solve(r, phi, prob)
+            assert rc == 0 and st["sweeps"] == steps
+            out[var, every] = phi.cpu().numpy()
+            assert _rel(out[var, every], ref) <= 5e-3, (var, every, _rel(out[var, every], ref))
+    assert np.array_equal(out[0, 1000], out[-1, 1000])
+    assert _rel(out[-1, 4], out[0, 4]) <= 1e-6
