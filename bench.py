@@ -467,10 +467,12 @@ def run(args):
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                     "unit": "GB/s", "frac": achieved / hbm_peak,
                     "traffic": recorded_traffic(), "peak_source": peak_src,
-                    "kernel": ("sweep_ws_kernel" if variant >= pk._pkr.pkr_batch_variant_count(
+                    "kernel": (("sweep_h16p_kernel" if variant == 1 else "sweep_h16_kernel")
+                               + f"<{LATTICE}>" if PRECISION == "fp16" else
+                               ("sweep_ws_kernel" if variant >= pk._pkr.pkr_batch_variant_count(
                                    pk.LATTICES[LATTICE]) else "sweep_staged_kernel") +
-                              f"<{LATTICE},"
-                              f"{ {'fp64': 'double', 'fx64': 'long long'}.get(PRECISION, 'float') }>",
+                               f"<{LATTICE},"
+                               f"{ {'fp64': 'double', 'fx64': 'long long'}.get(PRECISION, 'float') }>"),
                     "algorithmic_bytes_per_launch": V * bytes_site}
     if rank == 0:
         line = {
@@ -1032,7 +1034,8 @@ def run_pull_ceiling(args):
     out = {}
     for lattice in ("D3Q111", "D3Q19"):
         for elem in (8, 4):
-            for axes, label in ((0, "none"), (2, "yz"), (1, "x"), (3, "xyz")):
+            for axes, label in ((0, "none"), (2, "yz"), (1, "x"), (3, "xyz"),
+                                (7, "xyz_aligned_pairs")):
                 g = ctypes.c_double()
                 rc = pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES[lattice], n, elem, axes, 5,
                                                    ctypes.byref(g), None)

@@ -402,15 +402,19 @@ int pkr_ctx_destroy(pkr_ctx *ctx);
  * sweep's per-lane asynchronous copies of 32-site tiles into shared memory
  * and written back with streaming stores, in the staged sweep's default
  * geometry (2 velocity groups x 2 tiles per block of 4 warps), as many
- * blocks as fit.  shift_axes selects which components of the pull offsets -v_i are
- * kept: 0 none (a plain copy of Q planes), 1 x only, 2 y and z only, 3 all
- * (the sweep's pull).  Runs one untimed and `reps` timed copies on `stream`
+ * blocks as fit.  shift_axes selects which components of the pull offsets
+ * -v_i are kept: 0 none (a plain copy of Q planes), 1 x only, 2 y and z only,
+ * 3 all (the sweep's pull); 7 all, with the x offsets served from aligned
+ * runs (the block's two tiles x-adjacent, nx a multiple of 64: each
+ * velocity's two aligned 32-site blocks plus one aligned 4-site halo,
+ * shifted in shared memory; a staging the sweep does not use).  Runs one
+ * untimed and `reps` timed copies on `stream`
  * and returns, in *gbs, the bytes read and written per second (1e9 B/s).
  * It allocates 2 x Q x V x elem_bytes of device memory for the call.
  * lattice: PKR_D3Q19 or PKR_D3Q111; every edge at least the lattice's reach.
  * Errors: PKR_EINVAL (other lattices or element sizes, an edge below the
- * reach, V outside [1, 2^31 - 1], reps < 1, shift_axes outside 0..3),
- * PKR_ENOMEM, PKR_ECUDA.
+ * reach, V outside [1, 2^31 - 1], reps < 1, shift_axes not in 0..3 or 7,
+ * nx not a multiple of 64 for 7), PKR_ENOMEM, PKR_ECUDA.
  */
 int pkr_pull_copy_ceiling(int lattice, const int64_t n[3], int elem_bytes, int shift_axes,
                           int reps, double *gbs, void *stream);

@@ -19,6 +19,7 @@ namespace pkr {
 template <class L, typename T> int launch_sweep_t(int, const SweepArgs&, const void*, int, void*);
 template <class L, typename T> int occupancy_t(int, int*, int*);
 template <class L> int variant_count_t();
+template <class L> int pair_variant_t();
 template <class L> int launch_sweep_h16(int, const SweepArgs&, const void*, int, void*);
 template <class L> int occupancy_h16(int, int*, int*);
 template <class L>
@@ -51,14 +52,40 @@ int dispatch_occ(int var, int prec, int* b, int* tpb)
 
 int64_t tiles_of(const int64_t n[3]) { return (n[0] * n[1] * n[2] + 31) / 32; }
 
-// The two-sites-per-lane binary16 sweep applies: x rows of whole 64-site
-// tiles, every edge at least the lattice's reach.
-bool h16_pairs(const pkr_problem* p, const LatticeInfo& li)
+// The sweeps that work on 64-site pieces of x rows apply (the
+// two-sites-per-lane binary16 sweep and the aligned x-pairs sweep): x rows
+// of whole 64-site tiles, every edge at least the lattice's reach.
+bool x_pairs(const pkr_problem* p, const LatticeInfo& li)
 {
     if (p->n[0] % 64 != 0) return false;
     for (int k = 0; k < li.dim; ++k)
         if (p->n[k] < li.reach) return false;
     return true;
+}
+
+// Index of the aligned x-pairs variant of a lattice's plan sweep, or -1.
+int pair_variant(int lattice)
+{
+    switch (lattice) {
+    case PKR_D1Q5: return pair_variant_t<D1Q5>();
+    case PKR_D1Q9: return pair_variant_t<D1Q9>();
+    case PKR_D1Q13: return pair_variant_t<D1Q13>();
+    case PKR_D2Q25: return pair_variant_t<D2Q25>();
+    case PKR_D2Q81: return pair_variant_t<D2Q81>();
+    case PKR_D2Q169: return pair_variant_t<D2Q169>();
+    case PKR_D3Q19: return pair_variant_t<D3Q19>();
+    case PKR_D3Q111: return pair_variant_t<D3Q111>();
+    }
+    return -1;
+}
+
+int variant_count(int lattice);
+
+// The aligned x-pairs variants are the last ones of a lattice's list.
+bool is_pair_variant(int lattice, int variant)
+{
+    const int p = pair_variant(lattice);
+    return p >= 0 && variant >= p && variant < variant_count(lattice);
 }
 
 int variant_count(int lattice)
@@ -150,6 +177,7 @@ struct pkr_plan {
     // falling from one check to the next (the storage's rounding floor)
     double stall_cap;
     bool h16pairs;      // binary16 storage: the two-sites-per-lane sweep applies
+    bool xpairs;        // other storage: the aligned x-pairs sweep applies
     cudaStream_t stream;
     int device, grid, red_blocks, elem, small, variant, nsm;
     int64_t ntiles;
@@ -292,6 +320,8 @@ int launch_one(pkr_plan* P, int mode, bool zero_in)
             return PKR_ECUDA;
         return PKR_OK;
     }
+    // the aligned x-pairs sweep reads whole 64-site x pieces: never on other grids
+    if (is_pair_variant(P->prob.lattice, vr) && !P->xpairs) return PKR_EINVAL;
     switch (P->prob.lattice) {
     case PKR_D1Q5: rc = dispatch_launch<D1Q5>(vr, pr, a, c, P->grid, P->stream); break;
     case PKR_D1Q9: rc = dispatch_launch<D1Q9>(vr, pr, a, c, P->grid, P->stream); break;
@@ -348,6 +378,11 @@ int occupancy(int variant, int lattice, int precision, int* b, int* tpb)
 // of the largest grid any variant may use (allocated at plan creation).
 int set_variant(pkr_plan* P, int variant)
 {
+    // the aligned x-pairs geometry only where x rows split into 64-site
+    // pairs; elsewhere the staged 2 groups x 2 tiles (the same results)
+    if (P->prob.precision != PKR_FP16 && is_pair_variant(P->prob.lattice, variant) &&
+        !P->xpairs)
+        variant = 2;
     int bps = 0, tpb = 1;
     if (occupancy(variant, P->prob.lattice, P->prob.precision, &bps, &tpb) != 0 || bps < 1)
         return PKR_ECUDA;
@@ -571,7 +606,8 @@ int plan_create(const pkr_problem* p, void* stream, pkr_plan** out, bool spare)
     // binary16 storage: two sites per lane where every x row splits into
     // 64-site tiles (and no edge is below the reach), unless variant 0 (one
     // site per lane) is asked for; else one
-    P->h16pairs = p->precision == PKR_FP16 && h16_pairs(p, li);
+    P->h16pairs = p->precision == PKR_FP16 && x_pairs(p, li);
+    P->xpairs = p->precision != PKR_FP16 && x_pairs(p, li);
     if (p->precision == PKR_FP16) var = (P->h16pairs && p->variant != 0) ? 1 : 0;
     if (var >= nvar) {
         delete P;
@@ -811,6 +847,8 @@ int pkr_plan_autotune(pkr_plan* P, int steps_per_variant, int32_t* best_variant,
     float best_ms = 1e30f;
     int rc = PKR_OK;
     for (int v = 0; v < n && rc == PKR_OK; ++v) {
+        if (P->prob.precision != PKR_FP16 && is_pair_variant(P->prob.lattice, v) && !P->xpairs)
+            continue;   // the aligned x pairs need rows of whole 64-site pairs
         if (!P->stencil && (rc = set_variant(P, v)) != PKR_OK) break;
         if ((rc = launch_one(P, kPlain, false)) != PKR_OK) break;   // warm-up
         cudaEventRecord(e0, P->stream);
@@ -833,7 +871,7 @@ int pkr_plan_autotune(pkr_plan* P, int steps_per_variant, int32_t* best_variant,
     // keep the invariant that the latest Phi is written
     if ((rc = launch_one(P, kWritePhi, false)) != PKR_OK) return rc;
     PKR_CK(cudaStreamSynchronize(P->stream));
-    if (best_variant) *best_variant = best;
+    if (best_variant) *best_variant = P->stencil ? best : P->variant;
     if (best_ms_per_step) *best_ms_per_step = best_ms;
     return PKR_OK;
 }

@@ -91,6 +91,146 @@ pull_copy_kernel(const T* __restrict__ A, T* __restrict__ B, int64_t V, int nx, 
     }
 }
 
+// The pull with the x offsets served by aligned runs: the block's two tiles
+// are x-adjacent (64 sites of one row, nx a multiple of 64), warp (g, s)
+// copies the aligned 32-element block s of the pair for each velocity of
+// group g, plus one aligned 4-element halo on the side the velocity's x
+// component needs, into that velocity's 72-element row in shared memory;
+// after the two warps of the group meet, each reads its sites shifted by
+// -v_x from the row and stores them.  Per velocity and pair: two aligned
+// 256-byte runs and one 32-byte halo (five cache lines; six for two
+// shifted runs).
+template <class L, typename T>
+__global__ void __launch_bounds__(128)
+paired_copy_kernel(const T* __restrict__ A, T* __restrict__ B, int64_t V, int nx, int ny, int nz,
+                   int npairs)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int Q = L::Q;
+    constexpr int RC = reach_of<L>();
+    constexpr int W = 2 * RC + 1;
+    constexpr int RW = 72 * (int)sizeof(T);   // bytes of one velocity's row
+    static_assert(RC <= 4, "halo of 4 elements");
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int grp = w & 1;
+    const int sub = w >> 1;
+    const int nxy = nx * ny;
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        const int s0 = pr * 64;
+        const int r = (int)((unsigned)s0 / (unsigned)nx);
+        const int x0 = s0 - r * nx;
+        const int z = (int)((unsigned)r / (unsigned)ny);
+        const int y = r - z * ny;
+        int yo[W], zo[W];
+        static_for<0, W>([&](auto DI) {
+            constexpr int d = decltype(DI)::value - RC;
+            yo[d + RC] = wrap_off<d>(y, ny) * nx;
+            zo[d + RC] = wrap_off<d>(z, nz) * nxy;
+        });
+        const int xm = x0 + 32 * sub + lane;                       // aligned block s
+        const int xl = x0 >= 4 ? x0 - 4 + lane : nx - 4 + lane;   // left halo (lanes < 4)
+        const int xr = x0 + 64 < nx ? x0 + 64 + lane : lane;       // right halo (lanes < 4)
+        static_for<0, 2>([&](auto GI) {
+            constexpr int g = decltype(GI)::value;
+            constexpr int lo = g * Q / 2, hi = (g + 1) * Q / 2;
+            if (grp != g) return;
+            static_for<lo, hi>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int vx = vx_of<L>(i);
+                constexpr int oy = vy_of<L>(i) + RC;
+                constexpr int oz = vz_of<L>(i) + RC;
+                const T* row = A + ((int64_t)i * V + (zo[oz] + yo[oy]));
+                const uint32_t rb = base + (uint32_t)(i * RW);
+                cp_async<sizeof(T)>(rb + (uint32_t)((4 + 32 * sub + lane) * sizeof(T)), row + xm,
+                                    (int)sizeof(T));
+                if constexpr (vx > 0) {
+                    if (sub == 0 && lane < 4)
+                        cp_async<sizeof(T)>(rb + (uint32_t)(lane * sizeof(T)), row + xl,
+                                            (int)sizeof(T));
+                } else if constexpr (vx < 0) {
+                    if (sub == 1 && lane < 4)
+                        cp_async<sizeof(T)>(rb + (uint32_t)((68 + lane) * sizeof(T)), row + xr,
+                                            (int)sizeof(T));
+                }
+            });
+            cp_async_wait_all();
+            asm volatile("bar.sync %0, 64;" ::"r"(1 + g) : "memory");
+            T* dst = B + ((int64_t)lo * V + s0 + 32 * sub + lane);
+            static_for<lo, hi>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int vx = vx_of<L>(i);
+                const uint32_t ad =
+                    base + (uint32_t)(i * RW + (4 + 32 * sub + lane - vx) * (int)sizeof(T));
+                T v;
+                if constexpr (sizeof(T) == 8) {
+                    asm volatile("ld.shared.b64 %0, [%1];"
+                                 : "=l"(*reinterpret_cast<long long*>(&v)) : "r"(ad));
+                } else {
+                    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(*reinterpret_cast<int*>(&v))
+                                 : "r"(ad));
+                }
+                __stcs(dst, v);
+                dst += V;
+            });
+            // the rows are refilled for the next pair only after both warps read them
+            asm volatile("bar.sync %0, 64;" ::"r"(1 + g) : "memory");
+        });
+    }
+}
+
+template <class L, typename T>
+int run_paired_copy(const int64_t n[3], int reps, double* gbs, cudaStream_t st)
+{
+    const int64_t V = n[0] * n[1] * n[2];
+    const size_t bytes = (size_t)L::Q * (size_t)V * sizeof(T);
+    const int npairs = (int)(V / 64);
+    const size_t smem = (size_t)L::Q * 72 * sizeof(T);
+    auto kern = paired_copy_kernel<L, T>;
+    if (set_sweep_smem(kern, smem) != cudaSuccess) return PKR_ECUDA;
+    int dev = 0, nsm = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem) != cudaSuccess ||
+        occ < 1)
+        return PKR_ECUDA;
+    size_t freeb = 0, totb = 0;
+    if (cudaMemGetInfo(&freeb, &totb) != cudaSuccess) return PKR_ECUDA;
+    if (2 * bytes + (64 << 20) > freeb) return PKR_ENOMEM;
+    void *A = nullptr, *B = nullptr;
+    if (cudaMalloc(&A, bytes) != cudaSuccess || cudaMalloc(&B, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(A);
+        return PKR_ENOMEM;
+    }
+    int rc = PKR_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int grid = nsm * occ;
+    if (grid > npairs) grid = npairs;
+    if (cudaMemsetAsync(A, 0, bytes, st) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        rc = PKR_ECUDA;
+    for (int k = 0; rc == PKR_OK && k < reps + 1; ++k) {
+        if (k == 1 && cudaEventRecord(e0, st) != cudaSuccess) rc = PKR_ECUDA;
+        kern<<<grid, 128, smem, st>>>(static_cast<const T*>(A), static_cast<T*>(B), V, (int)n[0],
+                                     (int)n[1], (int)n[2], npairs);
+        if (cudaGetLastError() != cudaSuccess) rc = PKR_ECUDA;
+    }
+    float ms = 0.f;
+    if (rc == PKR_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                         cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = PKR_ECUDA;
+    if (rc == PKR_OK) *gbs = 2.0 * (double)bytes * reps / (ms * 1e-3) / 1e9;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(A);
+    cudaFree(B);
+    return rc;
+}
+
 template <class L, typename T, int SX, int SYZ>
 int run_pull_copy(const int64_t n[3], int reps, double* gbs, cudaStream_t st)
 {
@@ -99,9 +239,7 @@ int run_pull_copy(const int64_t n[3], int reps, double* gbs, cudaStream_t st)
     const int ntiles = (int)((V + 31) / 32);
     const size_t smem = (size_t)4 * ((L::Q + 1) / 2) * 32 * sizeof(T);
     auto kern = pull_copy_kernel<L, T, SX, SYZ>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return PKR_ECUDA;
+    if (set_sweep_smem(kern, smem) != cudaSuccess) return PKR_ECUDA;
     int dev = 0, nsm = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -152,6 +290,7 @@ int pull_copy_t(const int64_t n[3], int axes, int reps, double* gbs, cudaStream_
     case 1: return run_pull_copy<L, T, 1, 0>(n, reps, gbs, st);
     case 2: return run_pull_copy<L, T, 0, 1>(n, reps, gbs, st);
     case 3: return run_pull_copy<L, T, 1, 1>(n, reps, gbs, st);
+    case 7: return n[0] % 64 == 0 ? run_paired_copy<L, T>(n, reps, gbs, st) : PKR_EINVAL;
     }
     return PKR_EINVAL;
 }
@@ -174,7 +313,7 @@ extern "C" int pkr_pull_copy_ceiling(int lattice, const int64_t n[3], int elem_b
                                      int shift_axes, int reps, double* gbs, void* stream)
 {
     using namespace pkr;
-    if (!n || !gbs || reps < 1 || (shift_axes & ~3) != 0) return PKR_EINVAL;
+    if (!n || !gbs || reps < 1 || ((shift_axes & ~3) != 0 && shift_axes != 7)) return PKR_EINVAL;
     if (n[0] < 1 || n[1] < 1 || n[2] < 1) return PKR_EINVAL;
     const int64_t V = n[0] * n[1] * n[2];
     if (V > (int64_t)0x7fffffff) return PKR_EINVAL;

@@ -106,6 +106,27 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// 16-byte copy that is not kept in L1 (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async_cg16(uint32_t dst, const void* src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+// A sweep kernel's dynamic shared memory.  The split of each SM's L1/shared
+// array is left to the driver, which takes the smallest shared part that
+// holds the kernel's full occupancy: the rest stays L1, where the 4- and
+// 8-byte asynchronous copies of the pull land on their way to shared memory.
+// Forcing the largest shared part (228 KB, 28 KB of L1) measured 19% slower
+// for the staged sweep at 256^3 in 64-bit fixed point, whose three blocks
+// (60.5 KB each) fit the 196 KB split with 60 KB of L1.
+template <typename K>
+cudaError_t set_sweep_smem(K kern, size_t smem)
+{
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 // Launch geometry of the staged sweep.  A tile's Q velocities are split
 // among G warps (velocity groups): splitting cuts the shared memory a warp
 // stages by G and so lets an SM hold more warps, at the price of two
@@ -201,20 +222,20 @@ __device__ __forceinline__ long long fixed_term2(double v, int emax)
     return (long long)r ^ (long long)(hi >> 31);
 }
 
-// Largest exponent among N staged binary64 values (stride 256 B).
-template <int N>
+// Largest exponent among N staged binary64 values (VS bytes apart).
+template <int N, int VS = 256>
 __device__ __forceinline__ int max_exponent(uint32_t col)
 {
     int h0 = 0, h1 = 0;
 #pragma unroll 2
     for (int k = 0; k + 3 < N; k += 4) {
-        h0 = __vimax3_s32(h0, lds_hi32(col + (k + 0) * 256) & 0x7fffffff,
-                          lds_hi32(col + (k + 1) * 256) & 0x7fffffff);
-        h1 = __vimax3_s32(h1, lds_hi32(col + (k + 2) * 256) & 0x7fffffff,
-                          lds_hi32(col + (k + 3) * 256) & 0x7fffffff);
+        h0 = __vimax3_s32(h0, lds_hi32(col + (k + 0) * VS) & 0x7fffffff,
+                          lds_hi32(col + (k + 1) * VS) & 0x7fffffff);
+        h1 = __vimax3_s32(h1, lds_hi32(col + (k + 2) * VS) & 0x7fffffff,
+                          lds_hi32(col + (k + 3) * VS) & 0x7fffffff);
     }
 #pragma unroll
-    for (int k = N - N % 4; k < N; ++k) h0 = max(h0, lds_hi32(col + k * 256) & 0x7fffffff);
+    for (int k = N - N % 4; k < N; ++k) h0 = max(h0, lds_hi32(col + k * VS) & 0x7fffffff);
     return max(h0, h1) >> 20;
 }
 
@@ -224,7 +245,7 @@ __device__ __forceinline__ int max_exponent(uint32_t col)
 // rounded terms = (sum t_k + sum (t_k & 1)) / 2, exact, and even per partial).
 // |t_k| < 2^(54 + GB), so a partial of fewer than 2^(9 - GB) terms cannot
 // overflow; with GB = 10 - ceil(log2 Q) that holds for every N <= Q.
-template <int GB, int N>
+template <int GB, int N, int VS = 256>
 __device__ __forceinline__ long long fixed_sum(uint32_t col, int emax)
 {
     constexpr int U = 8;
@@ -234,7 +255,7 @@ __device__ __forceinline__ long long fixed_sum(uint32_t col, int emax)
     for (int k = 0; k + U - 1 < N; k += U) {
         double v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = lds_f64(col + (k + u) * 256);
+        for (int u = 0; u < U; ++u) v[u] = lds_f64(col + (k + u) * VS);
         long long t[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) t[u] = fixed_term2<GB>(v[u], emax);
@@ -246,7 +267,7 @@ __device__ __forceinline__ long long fixed_sum(uint32_t col, int emax)
     }
 #pragma unroll
     for (int k = N - N % U; k < N; ++k) {
-        const long long t = fixed_term2<GB>(lds_f64(col + k * 256), emax);
+        const long long t = fixed_term2<GB>(lds_f64(col + k * VS), emax);
         a[k % 4] += t;
         p[k % 4] += (int)(t & 1);
     }
@@ -254,11 +275,11 @@ __device__ __forceinline__ long long fixed_sum(uint32_t col, int emax)
            ((a[3] + p[3]) >> 1);
 }
 
-template <int N>
+template <int N, int VS = 256>
 __device__ __forceinline__ double plain_sum(uint32_t col)
 {
     double s = 0.0;
-    for (int k = 0; k < N; ++k) s += lds_f64(col + k * 256);
+    for (int k = 0; k < N; ++k) s += lds_f64(col + k * VS);
     return s;
 }
 
@@ -353,16 +374,23 @@ __device__ __forceinline__ double pow2(int e)
 // once otherwise; every meeting sits outside lane-dependent branches), the
 // relaxation and store of the group's velocities, and, in group 0, the
 // density output and the residual terms.  sbase: this lane's column of the
-// group's staged values (velocity lo(g) first, 32 values per velocity);
-// xacc, xexp: the tile's exchange rows.
-template <class L, typename T, int G, int g>
+// group's staged values (velocity lo(g) first, the next VS bytes further on);
+// xacc, xexp: the tile's exchange rows.  after_class(std::integral_constant
+// <int, cl>) runs, in every lane, once the group's velocities of symmetry
+// class cl are relaxed and stored (classes the group holds, in order).
+struct NoHook {
+    template <class C>
+    __device__ __forceinline__ void operator()(C) const {}
+};
+template <class L, typename T, int G, int g, int VS = 32 * (int)sizeof(T), class Hook = NoHook>
 __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
                                               const Coefs<typename AccType<T>::type>& c,
                                               int mode, bool valid, int s,
                                               typename AccType<T>::type Sx, int lane,
                                               uint32_t sbase, int bar, long long (&xacc)[G][32],
                                               int (&xexp)[G][32], double& d2, double& n2,
-                                              double& mx, double& ms, unsigned long long& fxm)
+                                              double& mx, double& ms, unsigned long long& fxm,
+                                              const Hook& after_class = Hook{})
 {
     using R = typename AccType<T>::type;
     constexpr int lo = g * L::Q / G;
@@ -377,7 +405,7 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
         // fixed point: the density is an exact integer sum
         long long part = 0;
 #pragma unroll 8
-        for (int k = 0; k < n; ++k) part += lds_s64(sbase + k * 256);
+        for (int k = 0; k < n; ++k) part += lds_s64(sbase + k * VS);
         if constexpr (G > 1) {
             xacc[g][lane] = part;
             asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
@@ -387,7 +415,7 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
         }
         Phi = (double)part * pow2(-tg.fr);
     } else if constexpr (std::is_same<T, double>::value) {
-        int emax = max_exponent<n>(sbase);
+        int emax = max_exponent<n, VS>(sbase);
         if constexpr (G > 1) {
             xexp[g][lane] = emax;
             asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
@@ -395,8 +423,8 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
             for (int k = 0; k < G; ++k) emax = max(emax, xexp[k][lane]);
         }
         const bool plain = plain_path(emax);
-        long long part = plain ? __double_as_longlong(plain_sum<n>(sbase))
-                               : fixed_sum<GB, n>(sbase, emax);
+        long long part = plain ? __double_as_longlong(plain_sum<n, VS>(sbase))
+                               : fixed_sum<GB, n, VS>(sbase, emax);
         if constexpr (G > 1) {
             xacc[g][lane] = part;
             asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
@@ -418,13 +446,13 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll 2
         for (int k = 0; k + 3 < n; k += 4) {
-            s0 += lds_f32(sbase + (k + 0) * 128);
-            s1 += lds_f32(sbase + (k + 1) * 128);
-            s2 += lds_f32(sbase + (k + 2) * 128);
-            s3 += lds_f32(sbase + (k + 3) * 128);
+            s0 += lds_f32(sbase + (k + 0) * VS);
+            s1 += lds_f32(sbase + (k + 1) * VS);
+            s2 += lds_f32(sbase + (k + 2) * VS);
+            s3 += lds_f32(sbase + (k + 3) * VS);
         }
 #pragma unroll
-        for (int k = n - n % 4; k < n; ++k) s0 += lds_f32(sbase + k * 128);
+        for (int k = n - n % 4; k < n; ++k) s0 += lds_f32(sbase + k * VS);
         float part = (s0 + s1) + (s2 + s3);
         if constexpr (G > 1) {
             // binary32 partials meet in group order (fixed, deterministic)
@@ -439,12 +467,12 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
 
     // relax and store this group's velocities, one symmetry class at a
     // time (velocities of a class are contiguous and share phi_c, chi_c)
-    if (valid) {
-        static_for<0, NC>([&](auto CI) {
-            constexpr int cl = decltype(CI)::value;
-            constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
-            constexpr int i0 = cb > lo ? cb : lo;
-            constexpr int i1 = ce < hi ? ce : hi;
+    static_for<0, NC>([&](auto CI) {
+        constexpr int cl = decltype(CI)::value;
+        constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
+        constexpr int i0 = cb > lo ? cb : lo;
+        constexpr int i1 = ce < hi ? ce : hi;
+        if (valid) {
             if constexpr (i0 < i1 && std::is_same<T, long long>::value) {
                 const double e = fma(c.wphi[cl], Phi, c.chi[cl] * Sx);
                 const long long ei = __double2ll_rn(e * pow2(tg.fw));
@@ -455,7 +483,7 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
                 T* dst = B + ((int64_t)i0 * V + s);
 #pragma unroll 4
                 for (int i = i0; i < i1; ++i) {
-                    const long long p = fx_mul(lds_s64(sbase + (i - lo) * 256), cw) + ei;
+                    const long long p = fx_mul(lds_s64(sbase + (i - lo) * VS), cw) + ei;
                     fxm |= (unsigned long long)(p ^ (p >> 63));
                     store_stream(dst, (T)p);
                     dst += V;
@@ -465,10 +493,10 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
                 T* dst = B + ((int64_t)i0 * V + s);
                 int i = i0;
                 for (; i + 3 < i1; i += 4) {
-                    const R g0 = lds_val<T>(sbase + (i + 0 - lo) * 32 * sizeof(T));
-                    const R g1 = lds_val<T>(sbase + (i + 1 - lo) * 32 * sizeof(T));
-                    const R g2 = lds_val<T>(sbase + (i + 2 - lo) * 32 * sizeof(T));
-                    const R g3 = lds_val<T>(sbase + (i + 3 - lo) * 32 * sizeof(T));
+                    const R g0 = lds_val<T>(sbase + (i + 0 - lo) * VS);
+                    const R g1 = lds_val<T>(sbase + (i + 1 - lo) * VS);
+                    const R g2 = lds_val<T>(sbase + (i + 2 - lo) * VS);
+                    const R g3 = lds_val<T>(sbase + (i + 3 - lo) * VS);
                     store_stream(dst, (T)fma(c.om1, g0, e));
                     store_stream(dst + V, (T)fma(c.om1, g1, e));
                     store_stream(dst + 2 * V, (T)fma(c.om1, g2, e));
@@ -476,13 +504,14 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
                     dst += 4 * V;
                 }
                 for (; i < i1; ++i) {
-                    const R gi = lds_val<T>(sbase + (i - lo) * 32 * sizeof(T));
+                    const R gi = lds_val<T>(sbase + (i - lo) * VS);
                     store_stream(dst, (T)fma(c.om1, gi, e));
                     dst += V;
                 }
             }
-        });
-    }
+        }
+        if constexpr (i0 < i1) after_class(CI);
+    });
     // density output and residual contributions (one group per tile)
     if (g == 0 && mode != kPlain && valid) {
         const double ph = (double)Phi;
@@ -709,7 +738,10 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     using ST = Staged<L, T, G, TILES>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double rpart[TILES][4];
-    __shared__ long long xacc[TILES][G][32];   // per-group partial densities of a tile
+    // per-group partial densities of a tile, two sets used by turns: a warp
+    // writes the next tile's partial only after the exchange barrier of that
+    // tile, so a partner still reading this tile's set cannot see it change
+    __shared__ long long xacc[2][TILES][G][32];
     __shared__ int xexp[TILES][G][32];         // per-group largest exponents
 
     const int lane = threadIdx.x & 31;
@@ -727,9 +759,10 @@ sweep_staged_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     double rd2 = 0.0, rn2 = 0.0, rmx = 0.0, rms = 0.0;
     unsigned long long fxm = 0ull;
     const int nt = gridDim.x * TILES;
-    for (int tile = blockIdx.x * TILES + sub; tile < a.ntiles; tile += nt)
+    int par = 0;
+    for (int tile = blockIdx.x * TILES + sub; tile < a.ntiles; tile += nt, par ^= 1)
         tile_step<L, T, G, TILES>(tg, c, tile, a.mode, a.zero_in != 0, lane, grp, sub, sbase,
-                                  xacc, xexp, rd2, rn2, rmx, rms, fxm);
+                                  xacc[par], xexp, rd2, rn2, rmx, rms, fxm);
     if constexpr (std::is_same<T, long long>::value) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -791,7 +824,7 @@ sweep_batch_kernel(BatchState* st, int K)
     constexpr int TILES = TILES_;
     using ST = Staged<L, T, G, TILES>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ long long xacc[TILES][G][32];
+    __shared__ long long xacc[2][TILES][G][32];   // two sets used by turns (staged sweep)
     __shared__ int xexp[TILES][G][32];
 
     const int lane = threadIdx.x & 31;
@@ -807,7 +840,8 @@ sweep_batch_kernel(BatchState* st, int K)
     double* tpart = st->tile_partials;
 
     const int nt = gridDim.x * TILES;
-    for (int tile = blockIdx.x * TILES + sub; tile < ntiles; tile += nt) {
+    int par = 0;
+    for (int tile = blockIdx.x * TILES + sub; tile < ntiles; tile += nt, par ^= 1) {
         int lo = 0, hi = ngrids - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -831,7 +865,7 @@ sweep_batch_kernel(BatchState* st, int K)
         double d2 = 0.0, n2 = 0.0, mx = 0.0, ms = 0.0;
         unsigned long long fxm = 0ull;
         tile_step<L, T, G, TILES>(tg, gd.c, tile - gd.tile_begin, mode, zero_in, lane, grp, sub,
-                                  sbase, xacc, xexp, d2, n2, mx, ms, fxm);
+                                  sbase, xacc[par], xexp, d2, n2, mx, ms, fxm);
         if constexpr (fx) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) fxm |= __shfl_down_sync(0xffffffffu, fxm, o);
@@ -871,8 +905,7 @@ int batch_occupancy_variant(int* blocks)
     constexpr Geo geo = Variants<L>::at(K);
     using ST = Staged<L, T, geo.G, geo.TILES>;
     auto kern = sweep_batch_kernel<L, T, geo.G, geo.TILES>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ST::smem_bytes());
+    cudaError_t e = set_sweep_smem(kern, ST::smem_bytes());
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, ST::WARPS * 32,
                                                               ST::smem_bytes());
@@ -1331,8 +1364,7 @@ int occupancy_h16(int variant, int* blocks, int* tiles_per_block)
 {
     const size_t smem = h16_smem<L>(variant);
     auto kern = variant == 1 ? sweep_h16p_kernel<L, kH16Tiles> : sweep_h16_kernel<L, kH16Tiles>;
-    cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_sweep_smem(kern, smem);
     if (e != cudaSuccess) return (int)e;
     // tiles_per_block counts 32-site tiles: a two-site tile is two of them
     *tiles_per_block = variant == 1 ? 2 * kH16Tiles : kH16Tiles;
@@ -1443,6 +1475,7 @@ int launch_stencil(const double* Pin, double* Pout, const double* St, const Coef
 
 }  // namespace pkr
 
+#include "pkr_sweep_pair.cuh"
 #include "pkr_sweep_ws.cuh"
 
 namespace pkr {
@@ -1465,8 +1498,7 @@ int occupancy_variant(int* blocks, int* tiles_per_block)
     constexpr Geo geo = Variants<L>::at(K);
     using ST = Staged<L, T, geo.G, geo.TILES>;
     auto kern = sweep_staged_kernel<L, T, geo.G, geo.TILES>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ST::smem_bytes());
+    cudaError_t e = set_sweep_smem(kern, ST::smem_bytes());
     if (e != cudaSuccess) return (int)e;
     *tiles_per_block = geo.TILES;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, ST::WARPS * 32,
@@ -1487,6 +1519,10 @@ int launch_sweep_t(int variant, const SweepArgs& a, const void* coefs, int grid,
         if (variant == Variants<L>::N + decltype(K)::value)
             rc = launch_ws_variant<L, T, decltype(K)::value>(a, coefs, grid, stream);
     });
+    static_for<0, PairVariant<L>::N>([&](auto K) {
+        if (variant == Variants<L>::N + WsVariants<L>::N + decltype(K)::value)
+            rc = launch_pair_variant<L, T, decltype(K)::value>(a, coefs, grid, stream);
+    });
     return rc;
 }
 
@@ -1502,13 +1538,21 @@ int occupancy_t(int variant, int* blocks, int* tiles_per_block)
         if (variant == Variants<L>::N + decltype(K)::value)
             rc = occupancy_ws_variant<L, T, decltype(K)::value>(blocks, tiles_per_block);
     });
+    static_for<0, PairVariant<L>::N>([&](auto K) {
+        if (variant == Variants<L>::N + WsVariants<L>::N + decltype(K)::value)
+            rc = occupancy_pair_variant<L, T, decltype(K)::value>(blocks, tiles_per_block);
+    });
     return rc;
 }
 
-// Variants of a plan's sweep (staged, then warp-specialised) and of the
-// batch sweep (staged only).
+// Variants of a plan's sweep (staged, warp-specialised, then the aligned x
+// pairs, which need nx a multiple of 64 and every edge at least the reach)
+// and of the batch sweep (staged only).
 template <class L>
-int variant_count_t() { return Variants<L>::N + WsVariants<L>::N; }
+int variant_count_t() { return Variants<L>::N + WsVariants<L>::N + PairVariant<L>::N; }
+// first aligned x-pairs variant (they are the last PairVariant<L>::N), or -1
+template <class L>
+int pair_variant_t() { return PairVariant<L>::N > 0 ? Variants<L>::N + WsVariants<L>::N : -1; }
 template <class L>
 int batch_variant_count_t() { return Variants<L>::N; }
 
@@ -1521,6 +1565,7 @@ int batch_variant_count_t() { return Variants<L>::N; }
     template int occupancy_t<L, float>(int, int*, int*);                                     \
     template int variant_count_t<L>();                                                      \
     template int batch_variant_count_t<L>();                                                \
+    template int pair_variant_t<L>();                                                       \
     template int launch_sweep_h16<L>(int, const SweepArgs&, const void*, int, void*);        \
     template int occupancy_h16<L>(int, int*, int*);                                          \
     template int launch_stencil<L>(const double*, double*, const double*, const Coefs<double>&,  \

@@ -1,0 +1,279 @@
+// pkr_sweep_pair.cuh -- the staged sweep with the pull's x offsets served
+// from aligned runs (included by pkr_sweep.cuh; same step, same arithmetic as
+// the 2 velocity groups x 2 tiles geometry, bit for bit).
+//
+// In the staged sweep every warp copies, for each velocity, the 32 values
+// x0 - v_x .. x0 - v_x + 31 of its row: for v_x != 0 the 256-byte run starts
+// off a 128-byte line and touches three lines, and the L1/L2 requests, not
+// DRAM, cap the sweep at about 0.72 of the copy peak for 111 velocities.
+// Here a block's two tiles are x-adjacent (64 sites of one row: nx a multiple
+// of 64).  For velocity i the group's two warps copy the two aligned 32-site
+// blocks x0 .. x0 + 63 of the velocity's source row, plus H aligned halo
+// values on the side v_x needs (x0 - H .. x0 - 1 for v_x > 0, x0 + 64 ..
+// x0 + 63 + H for v_x < 0; H = 4 for a reach of at most 4, else 8), into the
+// velocity's row of 64 + 2H values in shared memory, each value x written at
+// position H + (x - x0) + v_x.  Site x0 + p then finds its pulled value
+// x0 + p - v_x at position H + p: the rows read like the staged sweep's
+// columns, 64 + 2H values apart, and the density and relaxation code
+// (group_compute) runs unchanged.  The two warps of a velocity group meet at
+// a named barrier after the copies (each reads values the other copied) and
+// again before rows are refilled: after the whole pair, or, in the
+// early-refill form, after each symmetry class, whose rows then take the
+// block's next pair while the remaining classes are relaxed.
+#pragma once
+
+namespace pkr {
+
+template <class L, typename T>
+struct Pair {
+    static constexpr int Q = L::Q;
+    static constexpr int H = reach_of<L>();                // halo values per side
+    static constexpr int RL = 64 + 2 * H;                  // values per row
+    static constexpr int ROWB = RL * (int)sizeof(T);       // bytes per row
+    static constexpr size_t smem_bytes() { return (size_t)Q * ROWB; }
+    static_assert(sizeof(T) != 8 || ROWB % 16 == 0, "wide rows must start 16-byte aligned");
+    // 8-byte values of velocity i land 16-byte aligned in pairs (x0 + 2l,
+    // x0 + 2l + 1) when H + v_x is even: such a row is copied in 16-byte
+    // chunks that bypass L1, by one warp of the group
+    static constexpr bool wide(int i) { return sizeof(T) == 8 && ((H + vx_of<L>(i)) & 1) == 0; }
+    // wide rows among velocities lo .. i - 1 (the two warps take turns)
+    static constexpr int wide_rank(int lo, int i)
+    {
+        int n = 0;
+        for (int k = lo; k < i; ++k) n += wide(k) ? 1 : 0;
+        return n;
+    }
+    // halo of a wide row: HC values (whole chunks) on the side v_x needs
+    static constexpr int HC = 2 * ((H + 1) / 2);
+};
+
+// The pair geometry applies: x rows of whole 64-site pairs, every edge at
+// least the reach (the per-tile offsets wrap each side at most once).  Two
+// forms, both with 2 velocity groups: k = 0 fills a pair's rows, computes,
+// and only then fills the rows again for the block's next pair; k = 1
+// refills a symmetry class's rows for the next pair as soon as both warps of
+// the group have relaxed that class, so the copies of the next pair are in
+// flight while the rest of this pair is computed.
+template <class L>
+struct PairVariant {
+    static constexpr int N = (L::Q > 64) ? 2 : 0;
+    static constexpr int groups(int) { return 2; }
+    static constexpr bool early_refill(int k) { return k == 1; }
+};
+
+template <class L, typename T, int G, bool EARLY>
+__global__ void __launch_bounds__(64 * G)
+sweep_pair_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
+{
+    if (a.stop != nullptr && *a.stop != 0) return;   // the run stopped before this step
+    using R = typename AccType<T>::type;
+    using PR = Pair<L, T>;
+    constexpr int Q = L::Q;
+    constexpr int RC = reach_of<L>();
+    constexpr int W = 2 * RC + 1;
+    constexpr int H = PR::H;
+    constexpr int ROWB = PR::ROWB;
+    constexpr int ES = (int)sizeof(T);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double rpart[2][4];
+    // per-group partial densities of a tile, two sets used by turns (a warp
+    // writes the next pair's partial only after that pair's exchange barrier)
+    __shared__ long long xacc[2][2][G][32];
+    __shared__ int xexp[2][G][32];   // per-group largest exponents
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int grp = wib % G;     // velocity group of this warp
+    const int sub = wib / G;     // tile of the pair: sites x0 + 32 sub + lane
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const bool fx = std::is_same<T, long long>::value;
+    const T* __restrict__ A = static_cast<const T*>(a.A);
+    const TileGrid<T> tg{A, static_cast<T*>(a.B),
+                         static_cast<const typename SrcType<T>::type*>(a.S), a.Phi, a.V, a.nx,
+                         a.ny, a.nz, a.small, a.soff, fx ? a.fxF[a.cur] : 0,
+                         fx ? a.fxF[a.cur ^ 1] : 0, a.cfx};
+    const int64_t V = a.V;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int nxy = nx * ny;
+    const int npairs = (int)(V >> 6);
+    const int nbytes = a.zero_in ? 0 : ES;
+
+    constexpr int HC = PR::HC;
+    // the pair whose rows are being filled: its first x, the y and z row
+    // offsets of the pull, and this lane's halo positions: xl, xr one value
+    // per lane < H, wl, wr one 16-byte chunk per lane < HC / 2 (wide rows)
+    int yo[W], zo[W], fx0 = 0, xl = 0, xr = 0, wl = 0, wr = 0;
+    auto locate = [&](int p) {
+        const int s0 = p * 64;
+        const int r = (int)((unsigned)s0 / (unsigned)nx);
+        fx0 = s0 - r * nx;
+        const int z = (int)((unsigned)r / (unsigned)ny);
+        const int y = r - z * ny;
+        static_for<0, W>([&](auto DI) {
+            constexpr int d = decltype(DI)::value - RC;
+            yo[d + RC] = wrap_off<d>(y, ny) * nx;
+            zo[d + RC] = wrap_off<d>(z, nz) * nxy;
+        });
+        xl = (fx0 >= H ? fx0 - H : fx0 - H + nx) + lane;
+        xr = (fx0 + 64 < nx ? fx0 + 64 : 0) + lane;
+        wl = (fx0 >= HC ? fx0 - HC : fx0 - HC + nx) + 2 * lane;
+        wr = (fx0 + 64 < nx ? fx0 + 64 : 0) + 2 * lane;
+    };
+    // velocity i of that pair: value x goes to position H + (x - x0) + v_x of row i
+    auto pull = [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int vx = vx_of<L>(i);
+        constexpr int oy = vy_of<L>(i) + RC;
+        constexpr int oz = vz_of<L>(i) + RC;
+        const T* row = A + ((int64_t)i * V + (zo[oz] + yo[oy]));
+        const uint32_t rb = base + (uint32_t)(i * ROWB);
+        if constexpr (PR::wide(i)) {
+            // one warp: 32 chunks x0 + 2l, x0 + 2l + 1, and HC / 2 halo chunks
+            constexpr int owner = PR::wide_rank(0, i) & 1;
+            if (sub == owner) {
+                cp_async_cg16(rb + (uint32_t)((H + 2 * lane + vx) * ES), row + (fx0 + 2 * lane),
+                              2 * nbytes);
+                if constexpr (vx > 0) {
+                    if (lane < HC / 2)
+                        cp_async_cg16(rb + (uint32_t)((H - HC + vx + 2 * lane) * ES), row + wl,
+                                      2 * nbytes);
+                } else if constexpr (vx < 0) {
+                    if (lane < HC / 2)
+                        cp_async_cg16(rb + (uint32_t)((H + 64 + vx + 2 * lane) * ES), row + wr,
+                                      2 * nbytes);
+                }
+            }
+        } else {
+            cp_async<sizeof(T)>(rb + (uint32_t)((H + 32 * sub + lane + vx) * ES),
+                                row + (fx0 + 32 * sub + lane), nbytes);
+            if constexpr (vx > 0) {
+                if (sub == 0 && lane < H)
+                    cp_async<sizeof(T)>(rb + (uint32_t)((lane + vx) * ES), row + xl, nbytes);
+            } else if constexpr (vx < 0) {
+                if (sub == 1 && lane < H)
+                    cp_async<sizeof(T)>(rb + (uint32_t)((H + 64 + lane + vx) * ES), row + xr,
+                                        nbytes);
+            }
+        }
+    };
+
+    if constexpr (EARLY) {
+        if ((int)blockIdx.x < npairs) {
+            locate((int)blockIdx.x);
+            static_for<0, G>([&](auto GI) {
+                constexpr int g = decltype(GI)::value;
+                if (grp == g) static_for<g * Q / G, (g + 1) * Q / G>(pull);
+            });
+        }
+    }
+
+    double rd2 = 0.0, rn2 = 0.0, rmx = 0.0, rms = 0.0;
+    unsigned long long fxm = 0ull;
+    int par = 0;
+    for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x, par ^= 1) {
+        const int s = pr * 64 + 32 * sub + lane;   // this lane's site
+        // the source offset (mass correction) is used by binary32 storage only
+        R Sx;
+        if constexpr (std::is_same<T, float>::value) Sx = (R)((double)tg.S[s] + tg.soff);
+        else Sx = (R)tg.S[s];
+        const bool more = pr + (int)gridDim.x < npairs;   // the block has a next pair
+        if constexpr (EARLY) {
+            if (more) locate(pr + (int)gridDim.x);
+        } else {
+            locate(pr);
+        }
+
+        static_for<0, G>([&](auto GI) {
+            constexpr int g = decltype(GI)::value;
+            constexpr int lo = g * Q / G, hi = (g + 1) * Q / G;
+            if (grp != g) return;
+            if constexpr (!EARLY) static_for<lo, hi>(pull);
+            cp_async_wait_all();
+            // the group's other warp copied half of the values this one reads
+            asm volatile("bar.sync %0, 64;" ::"r"(3 + g) : "memory");
+            const uint32_t sb = base + (uint32_t)(lo * ROWB + (H + 32 * sub + lane) * ES);
+            if constexpr (EARLY) {
+                group_compute<L, T, G, g, ROWB>(
+                    tg, c, a.mode, true, s, Sx, lane, sb, 1 + sub, xacc[par][sub], xexp[sub], rd2,
+                    rn2, rmx, rms, fxm, [&](auto CI) {
+                        constexpr int cl = decltype(CI)::value;
+                        constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
+                        constexpr int i0 = cb > lo ? cb : lo;
+                        constexpr int i1 = ce < hi ? ce : hi;
+                        // both warps are done with the class's rows
+                        asm volatile("bar.sync %0, 64;" ::"r"(3 + g) : "memory");
+                        if (more) static_for<i0, i1>(pull);
+                    });
+            } else {
+                group_compute<L, T, G, g, ROWB>(tg, c, a.mode, true, s, Sx, lane, sb, 1 + sub,
+                                                xacc[par][sub], xexp[sub], rd2, rn2, rmx, rms,
+                                                fxm);
+                // both warps are done with the rows before either refills them
+                asm volatile("bar.sync %0, 64;" ::"r"(3 + g) : "memory");
+            }
+        });
+        __syncwarp();
+    }
+    if constexpr (std::is_same<T, long long>::value) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fxm |= __shfl_down_sync(0xffffffffu, fxm, o);
+        if (lane == 0 && fxm) atomicOr(a.fxmax, fxm);
+    }
+    if (a.mode == kCheck) {
+        if (grp == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                rd2 += __shfl_down_sync(0xffffffffu, rd2, o);
+                rn2 += __shfl_down_sync(0xffffffffu, rn2, o);
+                rmx = fmax(rmx, __shfl_down_sync(0xffffffffu, rmx, o));
+                rms += __shfl_down_sync(0xffffffffu, rms, o);
+            }
+            if (lane == 0) {
+                rpart[sub][0] = rd2;
+                rpart[sub][1] = rn2;
+                rpart[sub][2] = rmx;
+                rpart[sub][3] = rms;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+            for (int k = 0; k < 2; ++k) {
+                t0 += rpart[k][0];
+                t1 += rpart[k][1];
+                t2 = fmax(t2, rpart[k][2]);
+                t3 += rpart[k][3];
+            }
+            a.partials[4 * blockIdx.x + 0] = t0;
+            a.partials[4 * blockIdx.x + 1] = t1;
+            a.partials[4 * blockIdx.x + 2] = t2;
+            a.partials[4 * blockIdx.x + 3] = t3;
+        }
+    }
+}
+
+template <class L, typename T, int K>
+int launch_pair_variant(const SweepArgs& a, const void* coefs, int grid, void* stream)
+{
+    using R = typename AccType<T>::type;
+    constexpr int G = PairVariant<L>::groups(K);
+    constexpr bool EARLY = PairVariant<L>::early_refill(K);
+    sweep_pair_kernel<L, T, G, EARLY><<<grid, 64 * G, Pair<L, T>::smem_bytes(), (cudaStream_t)stream>>>(
+        a, *static_cast<const Coefs<R>*>(coefs));
+    return (int)cudaGetLastError();
+}
+
+template <class L, typename T, int K>
+int occupancy_pair_variant(int* blocks, int* tiles_per_block)
+{
+    constexpr int G = PairVariant<L>::groups(K);
+    constexpr bool EARLY = PairVariant<L>::early_refill(K);
+    auto kern = sweep_pair_kernel<L, T, G, EARLY>;
+    const size_t smem = Pair<L, T>::smem_bytes();
+    cudaError_t e = set_sweep_smem(kern, smem);
+    if (e != cudaSuccess) return (int)e;
+    *tiles_per_block = 2;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, 64 * G, smem);
+}
+
+}  // namespace pkr

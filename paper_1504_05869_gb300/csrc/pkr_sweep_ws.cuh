@@ -146,7 +146,7 @@ sweep_ws_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     constexpr int SP = WS::SPG;
     constexpr int ST = 32 * (int)sizeof(T);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ long long xacc[NG][G][32];   // per-group partial densities of a tile
+    __shared__ long long xacc[2][NG][G][32];   // per-group partial densities, two sets by turns
     __shared__ int xexp[NG][G][32];         // per-group largest exponents
     __shared__ double rpart[NG][4];
 
@@ -183,8 +183,8 @@ sweep_ws_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
                              a.cfx};
         double d2 = 0.0, n2 = 0.0, mx = 0.0, ms = 0.0;
         unsigned long long fxm = 0ull;
-        int sl = 0;
-        for (int j = g; j < nb; j += NG) {
+        int sl = 0, par = 0;
+        for (int j = g; j < nb; j += NG, par ^= 1) {
             const int f = g * SP + sl;
             const int tile = (int)blockIdx.x + j * (int)gridDim.x;
             const int64_t s64 = (int64_t)tile * 32 + lane;
@@ -206,7 +206,7 @@ sweep_ws_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
                 if (q == qq)
                     group_compute<L, T, G, qq>(tg, c, a.mode, valid, s, Sx, lane,
                                                sb + (uint32_t)((qq * L::Q / G) * ST),
-                                               1 + 2 * NS + g, xacc[g], xexp[g], d2, n2, mx, ms,
+                                               1 + 2 * NS + g, xacc[par][g], xexp[g], d2, n2, mx, ms,
                                                fxm);
             });
             __syncwarp();                               // lanes past the end rejoin
@@ -271,8 +271,7 @@ int occupancy_ws_variant(int* blocks, int* tiles_per_block)
     constexpr WsGeo geo = WsVariants<L>::at(K);
     using WS = Ws<L, T, geo.NG, geo.G, geo.SPG>;
     auto kern = sweep_ws_kernel<L, T, geo.NG, geo.G, geo.SPG>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)WS::smem_bytes());
+    cudaError_t e = set_sweep_smem(kern, WS::smem_bytes());
     if (e != cudaSuccess) return (int)e;
     *tiles_per_block = 1;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, WS::WARPS * 32,

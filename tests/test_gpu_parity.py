@@ -227,9 +227,11 @@ def _sampled_diffs(got, S, K, R, seed=12, count=300):
 # to 1e-13 / 1e-12 (a few ulps per step of values resolved to 2^-51 of the
 # largest), binary32 to 2e-5 (its parity bound).  Variant -1 is the default
 # launch configuration of the benchmark; 6 is the warp-specialised
-# sweep (3 groups of 4 compute warps, 2 slots each).
-FULL_CASES = [("fp64", -1, 1e-13), ("fp64", 6, 1e-13),
-              ("fx64", -1, 1e-12), ("fx64", 6, 1e-12), ("fp32", -1, 2e-5), ("fp32", 6, 2e-5)]
+# sweep (3 groups of 4 compute warps, 2 slots each), 7 the aligned x pairs,
+# 8 the aligned x pairs refilling each class's rows early.
+FULL_CASES = [("fp64", -1, 1e-13), ("fp64", 6, 1e-13), ("fp64", 7, 1e-13), ("fp64", 8, 1e-13),
+              ("fx64", -1, 1e-12), ("fx64", 6, 1e-12), ("fx64", 7, 1e-12), ("fx64", 8, 1e-12),
+              ("fp32", -1, 2e-5), ("fp32", 6, 2e-5), ("fp32", 7, 2e-5), ("fp32", 8, 2e-5)]
 
 
 @pytest.mark.slow
@@ -258,14 +260,28 @@ def test_full_size_256_sampled(pk, full_256, precision, variant, bar):
     ("D3Q111", 5, (29, 37, 41), "fp32"),
     ("D2Q169", 7, (287, 301), "fp64"),
     ("D2Q81", 5, (250, 330), "fx64"),
+    # x rows of whole 64-site pairs: the aligned x-pairs variant runs too
+    ("D3Q111", 5, (10, 12, 128), "fp64"),
+    ("D3Q111", 5, (10, 12, 128), "fx64"),
+    ("D3Q111", 5, (6, 5, 64), "fp32"),
+    ("D3Q111", 5, (3, 4, 192), "fp64"),
+    ("D2Q169", 7, (70, 64), "fp64"),
+    ("D2Q81", 5, (30, 128), "fx64"),
+    # several 64-site pairs per persistent block: the early refill of the
+    # next pair's rows runs, up to the last pair of each block
+    ("D3Q111", 5, (12, 20, 192), "fp64"),
+    ("D3Q111", 5, (16, 16, 256), "fx64"),
+    ("D3Q111", 5, (24, 24, 256), "fp32"),
 ])
 def test_every_variant_many_tiles_per_block(pk, lattice, order, shape, prec):
     """Grids of ~1400-2700 tiles with a ragged tail, so that every persistent
     block takes several tiles and the warp-specialised ring of tile slots is
-    reused many times.  Residual checks every 2 steps run inside the steps
-    (tol below reach: the run ends at max_sweeps).  Every variant matches the
-    oracle; binary64 and fixed-point variants agree bit for bit, and the
-    residuals they report agree to rounding."""
+    reused many times, and grids whose x rows split into 64-site pairs (the
+    aligned x-pairs variants, with halos wrapping at both ends of a row, y, z
+    edges down to the reach, and several pairs per block).  Residual checks every 2 steps run inside
+    the steps (tol below reach: the run ends at max_sweeps).  Every variant
+    matches the oracle; binary64 and fixed-point variants agree bit for bit,
+    and the residuals they report agree to rounding."""
     import torch
     rho = _rand(shape, 31)
     steps = 6
