@@ -142,16 +142,37 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def recorded_traffic():
+# the sources of the plan sweep kernels (the recorded traffic is void once they change)
+KERNEL_SOURCES = ("pkr_sweep.cuh", "pkr_sweep_pair.cuh", "pkr_sweep_ws.cuh", "pkr_lattices.h",
+                  "sweep_d3q111.cu")
+
+
+def kernel_label(pk, variant):
+    """Name of the sweep kernel a plan variant launches."""
+    T = {"fp64": "double", "fx64": "long long"}.get(PRECISION, "float")
+    if PRECISION == "fp16":
+        return ("sweep_h16p_kernel" if variant == 1 else "sweep_h16_kernel") + f"<{LATTICE}>"
+    nb = pk._pkr.pkr_batch_variant_count(pk.LATTICES[LATTICE])   # staged geometries
+    nv = pk._pkr.pkr_variant_count(pk.LATTICES[LATTICE])
+    if variant < nb:
+        return f"sweep_staged_kernel<{LATTICE},{T}>"
+    if nv - variant <= 2 and nv - nb == 3:
+        form = "early refill" if variant == nv - 1 else "refill after the pair"
+        return f"sweep_pair_kernel<{LATTICE},{T},G=2> ({form})"
+    return f"sweep_ws_kernel<{LATTICE},{T}>"
+
+
+def recorded_traffic(variant):
     """DRAM bytes per sweep launch of the headline workload from the committed
-    ncu summary, or None if the kernel sources changed since it was taken."""
+    ncu summary, or None if the kernel sources changed since it was taken or
+    the run launched another variant than the one captured."""
     import hashlib
     if (SHAPE, LATTICE, ORDER) != ((256, 256, 256), "D3Q111", 5) or \
             PRECISION not in ("fp64", "fx64"):
         return None
     csrc = os.path.join(ROOT, "paper_1504_05869_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("pkr_sweep.cuh", "pkr_lattices.h", "sweep_d3q111.cu"):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(csrc, f), "rb").read())
     try:
         txt = open(os.path.join(ROOT, "profiles",
@@ -159,8 +180,11 @@ def recorded_traffic():
     except OSError:
         return None
     vals = dict(line.split(": ", 1) for line in txt.splitlines()
-                if line.startswith(("traffic_bytes_per_launch_256cube", "source_sha256_16")))
+                if line.startswith(("traffic_bytes_per_launch_256cube", "source_sha256_16",
+                                    "kernel_variant")))
     if vals.get("source_sha256_16", "").strip() != h.hexdigest()[:16]:
+        return None
+    if vals.get("kernel_variant", "").strip() != str(variant):
         return None
     return float(vals["traffic_bytes_per_launch_256cube"])
 
@@ -466,13 +490,8 @@ def run(args):
     else:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                     "unit": "GB/s", "frac": achieved / hbm_peak,
-                    "traffic": recorded_traffic(), "peak_source": peak_src,
-                    "kernel": (("sweep_h16p_kernel" if variant == 1 else "sweep_h16_kernel")
-                               + f"<{LATTICE}>" if PRECISION == "fp16" else
-                               ("sweep_ws_kernel" if variant >= pk._pkr.pkr_batch_variant_count(
-                                   pk.LATTICES[LATTICE]) else "sweep_staged_kernel") +
-                               f"<{LATTICE},"
-                               f"{ {'fp64': 'double', 'fx64': 'long long'}.get(PRECISION, 'float') }>"),
+                    "traffic": recorded_traffic(variant), "peak_source": peak_src,
+                    "kernel": kernel_label(pk, variant),
                     "algorithmic_bytes_per_launch": V * bytes_site}
     if rank == 0:
         line = {
@@ -1022,7 +1041,8 @@ def run_tau1(args):
 def run_pull_ceiling(args):
     """Memory ceiling of the sweep's access pattern at 256^3 (pkr_pull_copy_
     ceiling): the bytes of one D3Q111 sweep moved with no arithmetic, through
-    the sweep's own staging, with the pull offsets kept per axis, for 8- and
+    the staged sweep's staging with the pull offsets kept per axis, through
+    aligned x pairs, and through the x-pairs sweep's own staging, for 8- and
     4-byte populations; beside D3Q19's."""
     import ctypes
     import torch
@@ -1035,7 +1055,7 @@ def run_pull_ceiling(args):
     for lattice in ("D3Q111", "D3Q19"):
         for elem in (8, 4):
             for axes, label in ((0, "none"), (2, "yz"), (1, "x"), (3, "xyz"),
-                                (7, "xyz_aligned_pairs")):
+                                (7, "xyz_aligned_pairs"), (8, "xyz_pair_sweep_staging")):
                 g = ctypes.c_double()
                 rc = pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES[lattice], n, elem, axes, 5,
                                                    ctypes.byref(g), None)

@@ -132,8 +132,11 @@ typedef struct pkr_problem {
                              a compiled variant (pkr_variant_count); in binary64 and
                              fixed point all variants give identical results (binary32
                              ones differ in rounding), they differ in speed.  -1 picks
-                             a geometry by grid size (more warps per tile on grids of
-                             a few tiles per SM).  With -1, a
+                             a geometry by grid size: the early-refill x-pairs sweep
+                             for sets of more than 64 velocities on grids of whole
+                             64-site x pairs with a few pairs per block (not D2Q169
+                             in fixed point), else 2 velocity groups x 2 tiles, or
+                             4 x 1 on grids of a few tiles per SM.  With -1, a
                              binary64 problem at tau_lb == 1 (omega = 1, the paper's
                              setting) runs as the scalar stencil Phi' = sum_i phi_i
                              Phi(x - v_i) + sum_i chi_i S(x - v_i): at omega = 1 the
@@ -179,7 +182,12 @@ int pkr_tau_from_knudsen(int lattice, double knudsen, const int64_t n[3], double
 /* Number of compiled sweep-kernel geometries of a plan for a lattice: the
  * staged ones (velocity groups per 32-site tile x tiles per block) first,
  * then, for sets of more than 64 velocities, the warp-specialised one (loader
- * warps filling a ring of tile slots, groups of compute warps draining it).
+ * warps filling a ring of tile slots, groups of compute warps draining it)
+ * and the two aligned x-pairs ones (64-site x pairs copied from aligned runs;
+ * the second refills each symmetry class's rows for the block's next pair as
+ * soon as that class is relaxed).  The x-pairs variants apply to grids whose
+ * x edge is a multiple of 64 and whose every edge is at least the reach;
+ * asked for on other grids, a plan takes the staged 2 x 2 geometry instead.
  * Host only; < 0 for an unknown lattice. */
 int pkr_variant_count(int lattice);
 
@@ -225,10 +233,12 @@ int pkr_plan_load_source(pkr_plan *plan, const double *rho, int rho_on_host);
 int pkr_plan_run(pkr_plan *plan, int64_t steps, double tol, int tol_kind, int check_every,
                  pkr_stats *stats);
 
-/* Autotuner: time every compiled sweep variant on the plan's own buffers
- * (one warm-up step, then `steps_per_variant` timed steps each, CUDA events on
- * the plan's stream) and keep the fastest.  The steps are real steps of the
- * solve: the plan advances by (1 + steps_per_variant) x count steps.  Must
+/* Autotuner: time every compiled sweep variant that applies to the plan's
+ * grid (the x-pairs variants only on grids of whole 64-site x pairs; see
+ * pkr_variant_count) on the plan's own buffers (one warm-up step, then
+ * `steps_per_variant` timed steps each, CUDA events on the plan's stream)
+ * and keep the fastest.  The steps are real steps of the solve: the plan
+ * advances by (1 + steps_per_variant) x (variants timed) steps.  Must
  * follow pkr_plan_load_source.  best_variant / best_ms_per_step may be NULL.
  * Synchronises. */
 int pkr_plan_autotune(pkr_plan *plan, int steps_per_variant, int32_t *best_variant,
@@ -404,17 +414,18 @@ int pkr_ctx_destroy(pkr_ctx *ctx);
  * geometry (2 velocity groups x 2 tiles per block of 4 warps), as many
  * blocks as fit.  shift_axes selects which components of the pull offsets
  * -v_i are kept: 0 none (a plain copy of Q planes), 1 x only, 2 y and z only,
- * 3 all (the sweep's pull); 7 all, with the x offsets served from aligned
- * runs (the block's two tiles x-adjacent, nx a multiple of 64: each
- * velocity's two aligned 32-site blocks plus one aligned 4-site halo,
- * shifted in shared memory; a staging the sweep does not use).  Runs one
- * untimed and `reps` timed copies on `stream`
+ * 3 all (the staged sweep's pull); 7 all, with the x offsets served from
+ * aligned runs (the block's two tiles x-adjacent, nx a multiple of 64: each
+ * velocity's two aligned 32-site blocks plus one aligned 4-site halo, per
+ * lane, read back shifted); 8 all, through the aligned x-pairs sweep's own
+ * staging (halo = the reach, values written shifted by v_x; nx a multiple
+ * of 64).  Runs one untimed and `reps` timed copies on `stream`
  * and returns, in *gbs, the bytes read and written per second (1e9 B/s).
  * It allocates 2 x Q x V x elem_bytes of device memory for the call.
  * lattice: PKR_D3Q19 or PKR_D3Q111; every edge at least the lattice's reach.
  * Errors: PKR_EINVAL (other lattices or element sizes, an edge below the
- * reach, V outside [1, 2^31 - 1], reps < 1, shift_axes not in 0..3 or 7,
- * nx not a multiple of 64 for 7), PKR_ENOMEM, PKR_ECUDA.
+ * reach, V outside [1, 2^31 - 1], reps < 1, shift_axes not in 0..3, 7 or 8,
+ * nx not a multiple of 64 for 7 and 8), PKR_ENOMEM, PKR_ECUDA.
  */
 int pkr_pull_copy_ceiling(int lattice, const int64_t n[3], int elem_bytes, int shift_axes,
                           int reps, double *gbs, void *stream);

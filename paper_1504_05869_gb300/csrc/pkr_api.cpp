@@ -103,17 +103,27 @@ int variant_count(int lattice)
     return -1;
 }
 
-// Default geometry per lattice, from timing every variant on GB300 at 256^3
-// (D3Q111: (2,2) fastest in binary64, 2.52 GLUPS, and binary32, 5.57 GLUPS;
-// D3Q19: the two variants within 0.2 %).  Index into the lattice's variant
-// list {(G,TILES)} = {(1,2),(2,1),(2,2),(3,1),(3,2),(4,1)} for Q > 64, else
-// {(1,2),(1,4)}: 2 velocity groups x 2 tiles for the large sets; on grids
-// with few tiles per SM, 4 groups x 1 tile (more warps share each tile, so
-// each step's chain is shorter).  All geometries give the same binary64 result.
-int default_variant(int lattice, int precision, int64_t V, int nsm)
+// Default geometry per lattice, from timing the variants on GB300.  Index
+// into the lattice's variant list: for Q > 64 the staged geometries
+// {(G,TILES)} = {(1,2),(2,1),(2,2),(3,1),(3,2),(4,1)}, the warp-specialised
+// sweep, then the aligned x-pairs sweep and its early-refill form; else
+// {(1,2),(1,4)} (D3Q19: the two within 0.2 %).  Large sets whose x rows are
+// whole 64-site pairs take the early-refill x-pairs sweep once the grid
+// gives every block a few pairs (GLUPS, early refill against (2,2): D3Q111
+// at 256^3 3.09 / 2.84 in 64-bit fixed point, 2.61 / 2.50 in binary64, 5.54
+// / 5.38 in binary32; D2Q81 at 2048^2 3.85 / 3.69 and 3.60 / 3.35; D2Q169 at
+// 2048^2 1.44 / 1.33 in binary64 but 1.35 / 1.48 in fixed point, where two
+// blocks of 103 KB per SM leave 28 KB of L1).  Other grids take 2 velocity
+// groups x 2 tiles, or, with few tiles per SM, 4 groups x 1 tile (more warps
+// share each tile, so each step's chain is shorter).  All geometries give
+// the same binary64 result.
+int default_variant(int lattice, int precision, int64_t V, int nsm, bool xpairs)
 {
-    (void)precision;
     if (variant_count(lattice) <= 2) return 0;
+    const int pv = pair_variant(lattice);
+    if (xpairs && pv >= 0 && V / 64 >= (int64_t)8 * nsm &&
+        !(lattice == PKR_D2Q169 && precision == PKR_FX64))
+        return pv + 1;
     return (V + 31) / 32 <= (int64_t)4 * nsm ? 5 : 2;
 }
 
@@ -602,12 +612,13 @@ int plan_create(const pkr_problem* p, void* stream, pkr_plan** out, bool spare)
     P->nsm = nsm;
     P->ntiles = tiles_of(p->n);
     const int nvar = variant_count(p->lattice);
-    int var = (p->variant >= 0) ? p->variant : default_variant(p->lattice, p->precision, P->V, nsm);
     // binary16 storage: two sites per lane where every x row splits into
     // 64-site tiles (and no edge is below the reach), unless variant 0 (one
     // site per lane) is asked for; else one
     P->h16pairs = p->precision == PKR_FP16 && x_pairs(p, li);
     P->xpairs = p->precision != PKR_FP16 && x_pairs(p, li);
+    int var = (p->variant >= 0) ? p->variant
+                                : default_variant(p->lattice, p->precision, P->V, nsm, P->xpairs);
     if (p->precision == PKR_FP16) var = (P->h16pairs && p->variant != 0) ? 1 : 0;
     if (var >= nvar) {
         delete P;

@@ -180,14 +180,64 @@ paired_copy_kernel(const T* __restrict__ A, T* __restrict__ B, int64_t V, int nx
     }
 }
 
+// The aligned x-pairs sweep's own staging (PairFill: halo = reach, values
+// written shifted by v_x), then each warp reads its sites at H + p of every
+// row of its group and stores them.  Same blocks and rows as the sweep, no
+// arithmetic, rows refilled after the pair.
 template <class L, typename T>
+__global__ void __launch_bounds__(128)
+sweep_staging_copy_kernel(const T* __restrict__ A, T* __restrict__ B, int64_t V, int nx, int ny,
+                          int nz, int npairs)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using PR = Pair<L, T>;
+    constexpr int Q = L::Q;
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int grp = w & 1;
+    const int sub = w >> 1;
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    PairFill<L, T> fill;
+    for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        fill.locate(pr, nx, ny, nz, lane);
+        static_for<0, 2>([&](auto GI) {
+            constexpr int g = decltype(GI)::value;
+            constexpr int lo = g * Q / 2, hi = (g + 1) * Q / 2;
+            if (grp != g) return;
+            static_for<lo, hi>([&](auto I) {
+                fill.template pull<decltype(I)::value>(A, V, base, sub, lane, (int)sizeof(T));
+            });
+            cp_async_wait_all();
+            asm volatile("bar.sync %0, 64;" ::"r"(1 + g) : "memory");
+            T* dst = B + ((int64_t)lo * V + pr * 64 + 32 * sub + lane);
+            static_for<lo, hi>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const uint32_t ad =
+                    base + (uint32_t)(i * PR::ROWB + (PR::H + 32 * sub + lane) * (int)sizeof(T));
+                T v;
+                if constexpr (sizeof(T) == 8) {
+                    asm volatile("ld.shared.b64 %0, [%1];"
+                                 : "=l"(*reinterpret_cast<long long*>(&v)) : "r"(ad));
+                } else {
+                    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(*reinterpret_cast<int*>(&v))
+                                 : "r"(ad));
+                }
+                __stcs(dst, v);
+                dst += V;
+            });
+            asm volatile("bar.sync %0, 64;" ::"r"(1 + g) : "memory");
+        });
+    }
+}
+
+template <class L, typename T, bool SWEEP>
 int run_paired_copy(const int64_t n[3], int reps, double* gbs, cudaStream_t st)
 {
     const int64_t V = n[0] * n[1] * n[2];
     const size_t bytes = (size_t)L::Q * (size_t)V * sizeof(T);
     const int npairs = (int)(V / 64);
-    const size_t smem = (size_t)L::Q * 72 * sizeof(T);
-    auto kern = paired_copy_kernel<L, T>;
+    const size_t smem = SWEEP ? Pair<L, T>::smem_bytes() : (size_t)L::Q * 72 * sizeof(T);
+    auto kern = SWEEP ? sweep_staging_copy_kernel<L, T> : paired_copy_kernel<L, T>;
     if (set_sweep_smem(kern, smem) != cudaSuccess) return PKR_ECUDA;
     int dev = 0, nsm = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -290,7 +340,8 @@ int pull_copy_t(const int64_t n[3], int axes, int reps, double* gbs, cudaStream_
     case 1: return run_pull_copy<L, T, 1, 0>(n, reps, gbs, st);
     case 2: return run_pull_copy<L, T, 0, 1>(n, reps, gbs, st);
     case 3: return run_pull_copy<L, T, 1, 1>(n, reps, gbs, st);
-    case 7: return n[0] % 64 == 0 ? run_paired_copy<L, T>(n, reps, gbs, st) : PKR_EINVAL;
+    case 7: return n[0] % 64 == 0 ? run_paired_copy<L, T, false>(n, reps, gbs, st) : PKR_EINVAL;
+    case 8: return n[0] % 64 == 0 ? run_paired_copy<L, T, true>(n, reps, gbs, st) : PKR_EINVAL;
     }
     return PKR_EINVAL;
 }
@@ -313,7 +364,8 @@ extern "C" int pkr_pull_copy_ceiling(int lattice, const int64_t n[3], int elem_b
                                      int shift_axes, int reps, double* gbs, void* stream)
 {
     using namespace pkr;
-    if (!n || !gbs || reps < 1 || ((shift_axes & ~3) != 0 && shift_axes != 7)) return PKR_EINVAL;
+    if (!n || !gbs || reps < 1 || ((shift_axes & ~3) != 0 && shift_axes != 7 && shift_axes != 8))
+        return PKR_EINVAL;
     if (n[0] < 1 || n[1] < 1 || n[2] < 1) return PKR_EINVAL;
     const int64_t V = n[0] * n[1] * n[2];
     if (V > (int64_t)0x7fffffff) return PKR_EINVAL;

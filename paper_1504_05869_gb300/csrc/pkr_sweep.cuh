@@ -106,14 +106,6 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// 16-byte copy that is not kept in L1 (both addresses 16-byte aligned)
-__device__ __forceinline__ void cp_async_cg16(uint32_t dst, const void* src, int src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
-                 "r"(src_bytes)
-                 : "memory");
-}
-
 // A sweep kernel's dynamic shared memory.  The split of each SM's L1/shared
 // array is left to the driver, which takes the smallest shared part that
 // holds the kernel's full occupancy: the rest stays L1, where the 4- and

@@ -8,11 +8,16 @@
 // DRAM, cap the sweep at about 0.72 of the copy peak for 111 velocities.
 // Here a block's two tiles are x-adjacent (64 sites of one row: nx a multiple
 // of 64).  For velocity i the group's two warps copy the two aligned 32-site
-// blocks x0 .. x0 + 63 of the velocity's source row, plus H aligned halo
-// values on the side v_x needs (x0 - H .. x0 - 1 for v_x > 0, x0 + 64 ..
-// x0 + 63 + H for v_x < 0; H = 4 for a reach of at most 4, else 8), into the
-// velocity's row of 64 + 2H values in shared memory, each value x written at
-// position H + (x - x0) + v_x.  Site x0 + p then finds its pulled value
+// blocks x0 .. x0 + 63 of the velocity's source row, plus H halo values on
+// the side v_x needs (x0 - H .. x0 - 1 for v_x > 0, x0 + 64 .. x0 + 63 + H
+// for v_x < 0; H = the lattice's reach), into the velocity's row of 64 + 2H
+// values in shared memory, each value x written at position H + (x - x0) +
+// v_x.  The rows are as short as the reach allows because the copies land
+// in L1 on their way to shared memory: with H = 3 three D3Q111 blocks of
+// 8-byte rows (62.2 KB + 2.1-2.6 KB of exchange rows each) fit the 196 KB
+// shared split of the SM and leave 60 KB of L1; with H = 4 they took the
+// 228 KB split (28 KB of L1), 13 % slower in 64-bit fixed point and 6 % in
+// binary64 (256^3, early refill).  Site x0 + p then finds its pulled value
 // x0 + p - v_x at position H + p: the rows read like the staged sweep's
 // columns, 64 + 2H values apart, and the density and relaxation code
 // (group_compute) runs unchanged.  The two warps of a velocity group meet at
@@ -31,20 +36,6 @@ struct Pair {
     static constexpr int RL = 64 + 2 * H;                  // values per row
     static constexpr int ROWB = RL * (int)sizeof(T);       // bytes per row
     static constexpr size_t smem_bytes() { return (size_t)Q * ROWB; }
-    static_assert(sizeof(T) != 8 || ROWB % 16 == 0, "wide rows must start 16-byte aligned");
-    // 8-byte values of velocity i land 16-byte aligned in pairs (x0 + 2l,
-    // x0 + 2l + 1) when H + v_x is even: such a row is copied in 16-byte
-    // chunks that bypass L1, by one warp of the group
-    static constexpr bool wide(int i) { return sizeof(T) == 8 && ((H + vx_of<L>(i)) & 1) == 0; }
-    // wide rows among velocities lo .. i - 1 (the two warps take turns)
-    static constexpr int wide_rank(int lo, int i)
-    {
-        int n = 0;
-        for (int k = lo; k < i; ++k) n += wide(k) ? 1 : 0;
-        return n;
-    }
-    // halo of a wide row: HC values (whole chunks) on the side v_x needs
-    static constexpr int HC = 2 * ((H + 1) / 2);
 };
 
 // The pair geometry applies: x rows of whole 64-site pairs, every edge at
@@ -61,6 +52,63 @@ struct PairVariant {
     static constexpr bool early_refill(int k) { return k == 1; }
 };
 
+// Filling the rows of one pair, in the warp (sub = tile of the pair) and
+// lane that run it: locate() takes the pair's first x, the y and z row
+// offsets of the pull and this lane's halo positions (one value per lane
+// < H); pull<i>() issues the copies of velocity i, value x to position
+// H + (x - x0) + v_x of row i (nbytes = 0: zero fill).  Every copy is one
+// value per lane: 16-byte chunks for the rows whose values land 16-byte
+// aligned (H + v_x even), copied past L1, measured no faster in 64-bit fixed
+// point and 4 % slower in binary64 at 256^3.
+template <class L, typename T>
+struct PairFill {
+    static constexpr int RC = reach_of<L>();
+    static constexpr int W = 2 * RC + 1;
+    static constexpr int H = Pair<L, T>::H;
+    static constexpr int ROWB = Pair<L, T>::ROWB;
+    static constexpr int ES = (int)sizeof(T);
+    int yo[W], zo[W];
+    int x0 = 0, xl = 0, xr = 0;
+
+    __device__ __forceinline__ void locate(int p, int nx, int ny, int nz, int lane)
+    {
+        const int s0 = p * 64;
+        const int r = (int)((unsigned)s0 / (unsigned)nx);
+        x0 = s0 - r * nx;
+        const int z = (int)((unsigned)r / (unsigned)ny);
+        const int y = r - z * ny;
+        const int nxy = nx * ny;
+        static_for<0, W>([&](auto DI) {
+            constexpr int d = decltype(DI)::value - RC;
+            yo[d + RC] = wrap_off<d>(y, ny) * nx;
+            zo[d + RC] = wrap_off<d>(z, nz) * nxy;
+        });
+        xl = (x0 >= H ? x0 - H : x0 - H + nx) + lane;
+        xr = (x0 + 64 < nx ? x0 + 64 : 0) + lane;
+    }
+
+    template <int i>
+    __device__ __forceinline__ void pull(const T* __restrict__ A, int64_t V, uint32_t base,
+                                         int sub, int lane, int nbytes) const
+    {
+        constexpr int vx = vx_of<L>(i);
+        constexpr int oy = vy_of<L>(i) + RC;
+        constexpr int oz = vz_of<L>(i) + RC;
+        const T* row = A + ((int64_t)i * V + (zo[oz] + yo[oy]));
+        const uint32_t rb = base + (uint32_t)(i * ROWB);
+        cp_async<sizeof(T)>(rb + (uint32_t)((H + 32 * sub + lane + vx) * ES),
+                            row + (x0 + 32 * sub + lane), nbytes);
+        if constexpr (vx > 0) {
+            if (sub == 0 && lane < H)
+                cp_async<sizeof(T)>(rb + (uint32_t)((lane + vx) * ES), row + xl, nbytes);
+        } else if constexpr (vx < 0) {
+            if (sub == 1 && lane < H)
+                cp_async<sizeof(T)>(rb + (uint32_t)((H + 64 + lane + vx) * ES), row + xr,
+                                    nbytes);
+        }
+    }
+};
+
 template <class L, typename T, int G, bool EARLY>
 __global__ void __launch_bounds__(64 * G)
 sweep_pair_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
@@ -69,8 +117,6 @@ sweep_pair_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
     using R = typename AccType<T>::type;
     using PR = Pair<L, T>;
     constexpr int Q = L::Q;
-    constexpr int RC = reach_of<L>();
-    constexpr int W = 2 * RC + 1;
     constexpr int H = PR::H;
     constexpr int ROWB = PR::ROWB;
     constexpr int ES = (int)sizeof(T);
@@ -94,72 +140,17 @@ sweep_pair_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
                          fx ? a.fxF[a.cur ^ 1] : 0, a.cfx};
     const int64_t V = a.V;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int nxy = nx * ny;
     const int npairs = (int)(V >> 6);
     const int nbytes = a.zero_in ? 0 : ES;
 
-    constexpr int HC = PR::HC;
-    // the pair whose rows are being filled: its first x, the y and z row
-    // offsets of the pull, and this lane's halo positions: xl, xr one value
-    // per lane < H, wl, wr one 16-byte chunk per lane < HC / 2 (wide rows)
-    int yo[W], zo[W], fx0 = 0, xl = 0, xr = 0, wl = 0, wr = 0;
-    auto locate = [&](int p) {
-        const int s0 = p * 64;
-        const int r = (int)((unsigned)s0 / (unsigned)nx);
-        fx0 = s0 - r * nx;
-        const int z = (int)((unsigned)r / (unsigned)ny);
-        const int y = r - z * ny;
-        static_for<0, W>([&](auto DI) {
-            constexpr int d = decltype(DI)::value - RC;
-            yo[d + RC] = wrap_off<d>(y, ny) * nx;
-            zo[d + RC] = wrap_off<d>(z, nz) * nxy;
-        });
-        xl = (fx0 >= H ? fx0 - H : fx0 - H + nx) + lane;
-        xr = (fx0 + 64 < nx ? fx0 + 64 : 0) + lane;
-        wl = (fx0 >= HC ? fx0 - HC : fx0 - HC + nx) + 2 * lane;
-        wr = (fx0 + 64 < nx ? fx0 + 64 : 0) + 2 * lane;
-    };
-    // velocity i of that pair: value x goes to position H + (x - x0) + v_x of row i
+    PairFill<L, T> fill;   // the pair whose rows are being filled
     auto pull = [&](auto I) {
-        constexpr int i = decltype(I)::value;
-        constexpr int vx = vx_of<L>(i);
-        constexpr int oy = vy_of<L>(i) + RC;
-        constexpr int oz = vz_of<L>(i) + RC;
-        const T* row = A + ((int64_t)i * V + (zo[oz] + yo[oy]));
-        const uint32_t rb = base + (uint32_t)(i * ROWB);
-        if constexpr (PR::wide(i)) {
-            // one warp: 32 chunks x0 + 2l, x0 + 2l + 1, and HC / 2 halo chunks
-            constexpr int owner = PR::wide_rank(0, i) & 1;
-            if (sub == owner) {
-                cp_async_cg16(rb + (uint32_t)((H + 2 * lane + vx) * ES), row + (fx0 + 2 * lane),
-                              2 * nbytes);
-                if constexpr (vx > 0) {
-                    if (lane < HC / 2)
-                        cp_async_cg16(rb + (uint32_t)((H - HC + vx + 2 * lane) * ES), row + wl,
-                                      2 * nbytes);
-                } else if constexpr (vx < 0) {
-                    if (lane < HC / 2)
-                        cp_async_cg16(rb + (uint32_t)((H + 64 + vx + 2 * lane) * ES), row + wr,
-                                      2 * nbytes);
-                }
-            }
-        } else {
-            cp_async<sizeof(T)>(rb + (uint32_t)((H + 32 * sub + lane + vx) * ES),
-                                row + (fx0 + 32 * sub + lane), nbytes);
-            if constexpr (vx > 0) {
-                if (sub == 0 && lane < H)
-                    cp_async<sizeof(T)>(rb + (uint32_t)((lane + vx) * ES), row + xl, nbytes);
-            } else if constexpr (vx < 0) {
-                if (sub == 1 && lane < H)
-                    cp_async<sizeof(T)>(rb + (uint32_t)((H + 64 + lane + vx) * ES), row + xr,
-                                        nbytes);
-            }
-        }
+        fill.template pull<decltype(I)::value>(A, V, base, sub, lane, nbytes);
     };
 
     if constexpr (EARLY) {
         if ((int)blockIdx.x < npairs) {
-            locate((int)blockIdx.x);
+            fill.locate((int)blockIdx.x, nx, ny, nz, lane);
             static_for<0, G>([&](auto GI) {
                 constexpr int g = decltype(GI)::value;
                 if (grp == g) static_for<g * Q / G, (g + 1) * Q / G>(pull);
@@ -178,9 +169,9 @@ sweep_pair_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
         else Sx = (R)tg.S[s];
         const bool more = pr + (int)gridDim.x < npairs;   // the block has a next pair
         if constexpr (EARLY) {
-            if (more) locate(pr + (int)gridDim.x);
+            if (more) fill.locate(pr + (int)gridDim.x, nx, ny, nz, lane);
         } else {
-            locate(pr);
+            fill.locate(pr, nx, ny, nz, lane);
         }
 
         static_for<0, G>([&](auto GI) {

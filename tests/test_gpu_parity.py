@@ -339,6 +339,27 @@ def test_every_kernel_variant(pk, lattice, order, shape, prec):
             assert np.array_equal(o, outs[0])
 
 
+def test_autotune_on_whole_x_pairs_times_every_variant(pk):
+    """On a grid of whole 64-site x pairs every compiled variant is timed,
+    the x-pairs ones included, and the solve continues from the steps taken."""
+    import torch
+    rho = _rand((5, 6, 64), 24)   # (nz, ny, nx)
+    prob = pk.problem("D3Q111", rho.shape, 5, tau_lb=1.2, max_sweeps=100, precision="fx64")
+    r = torch.from_numpy(rho).cuda()
+    out = torch.empty_like(r)
+    n = pk._pkr.pkr_variant_count(pk.LATTICES["D3Q111"])
+    with pk.Plan(prob) as P:
+        P.load_source(r)
+        best, ms = P.autotune(1)
+        assert 0 <= best < n and ms > 0
+        t = P.steps()
+        assert t == (1 + 1) * n + 1
+        P.run(2)
+        P.phi(out)
+    ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.2, max_steps=t + 2).phi
+    assert _rel(out.cpu().numpy(), ref) <= FP64_TOL
+
+
 def test_autotune_advances_real_steps(pk):
     import torch
     rho = _rand((16, 12, 20), 14)
@@ -346,12 +367,14 @@ def test_autotune_advances_real_steps(pk):
     r = torch.from_numpy(rho).cuda()
     out = torch.empty_like(r)
     n = pk._pkr.pkr_variant_count(pk.LATTICES["D3Q111"])
+    # x edge 20: the two aligned x-pairs variants do not apply and are skipped
+    timed = n - 2
     with pk.Plan(prob) as P:
         P.load_source(r)
         best, ms = P.autotune(2)
-        assert 0 <= best < n and ms > 0
+        assert 0 <= best < timed and ms > 0
         t = P.steps()
-        assert t == (1 + 2) * n + 1
+        assert t == (1 + 2) * timed + 1
         P.run(3)
         P.phi(out)
     ref = oracle.solve(rho, "D3Q111", 5, tau_lb=1.2, max_steps=t + 3).phi
@@ -624,7 +647,19 @@ def test_pull_copy_ceiling_diagnostic(pk):
         assert g.value > 100.0
         got[axes] = g.value
     assert got[3] <= 1.1 * got[2]
+    # aligned x pairs and the x-pairs sweep's own staging (16-byte chunks for
+    # the rows that land aligned), 8- and 4-byte values, both large sets
+    for lattice in ("D3Q111", "D3Q19"):
+        for elem in (8, 4):
+            for axes in (7, 8):
+                g = ctypes.c_double()
+                assert pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES[lattice], n, elem, axes, 3,
+                                                     ctypes.byref(g), None) == 0
+                assert g.value > 100.0
     g = ctypes.c_double()
+    n48 = (ctypes.c_int64 * 3)(48, 64, 64)
+    assert pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES["D3Q111"], n48, 8, 8, 3, ctypes.byref(g),
+                                         None) == pk._pkr.PKR_EINVAL
     assert pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES["D2Q169"], n, 8, 3, 3, ctypes.byref(g),
                                          None) == pk._pkr.PKR_EINVAL
     assert pk._pkr.pkr_pull_copy_ceiling(pk.LATTICES["D3Q111"], n, 2, 3, 3, ctypes.byref(g),
