@@ -344,6 +344,26 @@ __device__ __forceinline__ long long lds_s64(uint32_t addr)
     return v;
 }
 
+// Sum of N staged 64-bit fixed-point values (VS bytes apart) in four
+// interleaved partials: integer addition is exact and associative (two's
+// complement wraps cancel), so the split leaves the sum unchanged and cuts
+// the dependent chain of 64-bit adds to a quarter.
+template <int N, int VS>
+__device__ __forceinline__ long long fx_sum(uint32_t col)
+{
+    long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll 2
+    for (int k = 0; k + 3 < N; k += 4) {
+        a0 += lds_s64(col + (k + 0) * VS);
+        a1 += lds_s64(col + (k + 1) * VS);
+        a2 += lds_s64(col + (k + 2) * VS);
+        a3 += lds_s64(col + (k + 3) * VS);
+    }
+#pragma unroll
+    for (int k = N - N % 4; k < N; ++k) a0 += lds_s64(col + k * VS);
+    return (a0 + a1) + (a2 + a3);
+}
+
 // round(q c / 2^62), rounding half up (c = (1 - omega) 2^62 for the relaxation)
 __device__ __forceinline__ long long fx_mul(long long q, long long c)
 {
@@ -395,9 +415,7 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
     R Phi;
     if constexpr (std::is_same<T, long long>::value) {
         // fixed point: the density is an exact integer sum
-        long long part = 0;
-#pragma unroll 8
-        for (int k = 0; k < n; ++k) part += lds_s64(sbase + k * VS);
+        long long part = fx_sum<n, VS>(sbase);
         if constexpr (G > 1) {
             xacc[g][lane] = part;
             asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
@@ -596,9 +614,7 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
         R Phi;
         if constexpr (std::is_same<T, long long>::value) {
             // fixed point: the density is an exact integer sum
-            long long part = 0;
-#pragma unroll 8
-            for (int k = 0; k < n; ++k) part += lds_s64(sbase + k * 256);
+            long long part = fx_sum<n, 256>(sbase);
             if constexpr (G > 1) {
                 xacc[sub][g][lane] = part;
                 asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
