@@ -367,8 +367,9 @@ def test_autotune_advances_real_steps(pk):
     r = torch.from_numpy(rho).cuda()
     out = torch.empty_like(r)
     n = pk._pkr.pkr_variant_count(pk.LATTICES["D3Q111"])
-    # x edge 20: the two aligned x-pairs variants do not apply and are skipped
-    timed = n - 2
+    # x edge 20: the aligned x-pairs variants (after the staged geometries and
+    # the warp-specialised one) do not apply and are skipped
+    timed = pk._pkr.pkr_batch_variant_count(pk.LATTICES["D3Q111"]) + 1
     with pk.Plan(prob) as P:
         P.load_source(r)
         best, ms = P.autotune(2)
