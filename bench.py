@@ -1083,8 +1083,8 @@ def main():
                     help="skip the time-to-1e-8 and serving objects of the default line")
     ap.add_argument("--serve-requests", type=int, default=500,
                     help="default line: arrivals of the 200/s serving trace")
-    ap.add_argument("--serve-sub-requests", type=int, default=16)
-    ap.add_argument("--serve-sub-rate", type=float, default=1.0)
+    ap.add_argument("--serve-sub-requests", type=int, default=100)
+    ap.add_argument("--serve-sub-rate", type=float, default=2.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--size", type=int, default=0, help="cube edge (default 256)")
     ap.add_argument("--lattice", default="D3Q111", choices=["D3Q111", "D3Q19"])
