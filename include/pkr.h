@@ -154,6 +154,11 @@ typedef struct pkr_stats {
     double wall_ms;          /* host wall time of the call */
     double glups;            /* site updates / wall time, 1e9 / s */
     double hbm_gbs;          /* algorithmic bytes / wall time, GB/s */
+    int32_t variant;         /* sweep geometry that ran (its last plan, for a precision
+                                ladder): an index into the list pkr_variant_count counts
+                                (pkr_batch_variant_count for a context's request; binary16:
+                                0 one site per lane, 1 two); -1 when no population sweep
+                                ran (scalar stencil, pkr_fixed_point_fft) */
 } pkr_stats;
 
 /* Human-readable name of a status code (static string). */

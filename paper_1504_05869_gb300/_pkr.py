@@ -53,7 +53,7 @@ class pkr_stats(ctypes.Structure):
                 ("residual", ctypes.c_double), ("rho_mean_removed", ctypes.c_double),
                 ("tau_lb", ctypes.c_double), ("cs2", ctypes.c_double),
                 ("wall_ms", ctypes.c_double), ("glups", ctypes.c_double),
-                ("hbm_gbs", ctypes.c_double)]
+                ("hbm_gbs", ctypes.c_double), ("variant", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

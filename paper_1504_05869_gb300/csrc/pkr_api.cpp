@@ -1082,6 +1082,7 @@ int pkr_plan_run(pkr_plan* P, int64_t steps, double tol, int tol_kind, int check
         st->glups = ms > 0 ? upd / (ms * 1e6) : 0.0;
         const double bytes_site = 2.0 * P->lat.Q * P->elem + source_bytes(P->prob.precision);
         st->hbm_gbs = ms > 0 ? upd * bytes_site / (ms * 1e6) : 0.0;
+        st->variant = P->stencil ? -1 : P->variant;
     }
     return status;
 }

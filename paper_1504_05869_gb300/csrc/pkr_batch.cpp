@@ -611,6 +611,7 @@ int retire(pkr_ctx* C, int ln, long long step0)
         j->st.rho_mean_removed = j->mean;
         j->st.tau_lb = j->tau;
         j->st.cs2 = C->li.cs2;
+        j->st.variant = L.variant;
         if (status == PKR_OK || status == PKR_ENOCONV) {
             if (cudaMemcpyAsync(j->phi, j->Phi, (size_t)j->V * 8,
                                 j->host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,

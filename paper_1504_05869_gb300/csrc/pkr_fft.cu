@@ -244,6 +244,7 @@ extern "C" int pkr_fixed_point_fft(const pkr_problem* p, const double* rho, doub
         st->cs2 = li.cs2;
         st->wall_ms = ms;
         st->residual = 0.0;
+        st->variant = -1;
     }
     return PKR_OK;
 }

@@ -82,6 +82,8 @@ def test_batch_matches_oracle(pk, precision, bar):
         assert rc == 0, rc
         assert st["residual"] < tol
         assert (st["sweeps"] + 1) % 8 == 0
+        # the batch geometry that ran, from the context's own list
+        assert 0 <= st["variant"] < pk._pkr.pkr_batch_variant_count(pk.LATTICES["D3Q111"])
         ref = oracle.solve(rho, "D3Q111", 5, tau_lb=tau, max_steps=st["sweeps"]).phi
         assert _rel(got, ref) <= bar, (rho.shape, _rel(got, ref))
         assert abs(st["rho_mean_removed"] - rho.mean()) < 1e-15

@@ -694,3 +694,41 @@ def test_fp16_two_sites_per_lane(pk, lattice, order, shape, tau):
             assert _rel(out[var, every], ref) <= 5e-3, (var, every, _rel(out[var, every], ref))
     assert np.array_equal(out[0, 1000], out[-1, 1000])
     assert _rel(out[-1, 4], out[0, 4]) <= 1e-6
+
+
+def test_default_geometry_and_reported_variant(pk):
+    """With variant -1 a plan takes the early-refill aligned x-pairs sweep
+    (the last variant) on grids of whole 64-site x rows with at least 8
+    pairs per SM, the staged 2 x 2 geometry on other grids, 4 x 1 on grids
+    of at most 4 tiles per SM, the staged sweep for D2Q169 in fixed point,
+    and the scalar stencil (reported as -1) for binary64 at tau_lb = 1; the
+    stats report the geometry that ran, and each result matches the oracle."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    n3 = pk._pkr.pkr_variant_count(pk.LATTICES["D3Q111"])
+    n2 = pk._pkr.pkr_variant_count(pk.LATTICES["D2Q169"])
+    nz = -(-8 * nsm * 64 // (64 * 64))       # enough 64 x 64 planes for 8 pairs per SM
+    cases = [
+        ("D3Q111", 5, (nz, 64, 64), "fx64", 1.3, n3 - 1),
+        ("D3Q111", 5, (nz, 64, 60), "fp64", 1.3, 2),
+        ("D3Q111", 5, (6, 5, 64), "fx64", 1.3, 5),
+        ("D2Q169", 7, (8 * nsm * 64 // 2048 + 1, 2048), "fx64", 1.3, 2),
+        ("D2Q169", 7, (8 * nsm * 64 // 2048 + 1, 2048), "fp64", 1.3, n2 - 1),
+        ("D3Q111", 5, (6, 5, 64), "fp64", 1.0, -1),
+    ]
+    for lattice, order, shape, prec, tau, want in cases:
+        rho = _rand(shape, 41)
+        steps = 3
+        prob = pk.problem(lattice, shape, order, tau_lb=tau, max_sweeps=steps, precision=prec)
+        r = torch.from_numpy(rho).cuda()
+        phi = torch.empty_like(r)
+        rc, st = pk.solve(r, phi, prob)
+        assert rc == 0 and st["sweeps"] == steps, (lattice, shape, prec, rc)
+        assert st["variant"] == want, (lattice, shape, prec, st["variant"], want)
+        ref = oracle.solve(rho, lattice, order, tau_lb=tau, max_steps=steps).phi
+        assert _rel(phi.cpu().numpy(), ref) <= FP64_TOL, (lattice, shape, prec)
+    rho = _rand((6, 5, 64), 42)
+    r = torch.from_numpy(rho).cuda()
+    fx = torch.empty_like(r)
+    st = pk.fixed_point_fft(r, fx, pk.problem("D3Q111", rho.shape, 5, tau_lb=1.3))
+    assert st["variant"] == -1
