@@ -347,12 +347,13 @@ __device__ __forceinline__ long long lds_s64(uint32_t addr)
 // Sum of N staged 64-bit fixed-point values (VS bytes apart) in four
 // interleaved partials: integer addition is exact and associative (two's
 // complement wraps cancel), so the split leaves the sum unchanged and cuts
-// the dependent chain of 64-bit adds to a quarter.
-template <int N, int VS>
+// the dependent chain of 64-bit adds to a quarter.  U: groups of four per
+// loop trip (code size against loop overhead; timed per kernel at 256^3).
+template <int N, int VS, int U>
 __device__ __forceinline__ long long fx_sum(uint32_t col)
 {
     long long a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-#pragma unroll 2
+#pragma unroll U
     for (int k = 0; k + 3 < N; k += 4) {
         a0 += lds_s64(col + (k + 0) * VS);
         a1 += lds_s64(col + (k + 1) * VS);
@@ -415,7 +416,7 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
     R Phi;
     if constexpr (std::is_same<T, long long>::value) {
         // fixed point: the density is an exact integer sum
-        long long part = fx_sum<n, VS>(sbase);
+        long long part = fx_sum<n, VS, 1>(sbase);
         if constexpr (G > 1) {
             xacc[g][lane] = part;
             asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
@@ -491,7 +492,7 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
                 const int k = tg.fr - tg.fw;
                 const long long cw = k == 0 ? tg.cfx : ((tg.cfx >> (k - 1)) + 1) >> 1;
                 T* dst = B + ((int64_t)i0 * V + s);
-#pragma unroll 4
+#pragma unroll 2
                 for (int i = i0; i < i1; ++i) {
                     const long long p = fx_mul(lds_s64(sbase + (i - lo) * VS), cw) + ei;
                     fxm |= (unsigned long long)(p ^ (p >> 63));
@@ -614,7 +615,7 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
         R Phi;
         if constexpr (std::is_same<T, long long>::value) {
             // fixed point: the density is an exact integer sum
-            long long part = fx_sum<n, 256>(sbase);
+            long long part = fx_sum<n, 256, 4>(sbase);
             if constexpr (G > 1) {
                 xacc[sub][g][lane] = part;
                 asm volatile("bar.sync %0, %1;" ::"r"(1 + sub), "n"(G * 32) : "memory");
@@ -690,7 +691,7 @@ __device__ __forceinline__ void tile_step(const TileGrid<T>& tg,
                     const int k = tg.fr - tg.fw;
                     const long long cw = k == 0 ? tg.cfx : ((tg.cfx >> (k - 1)) + 1) >> 1;
                     T* dst = B + ((int64_t)i0 * V + s);
-#pragma unroll 4
+#pragma unroll 2
                     for (int i = i0; i < i1; ++i) {
                         const long long p = fx_mul(lds_s64(sbase + (i - lo) * 256), cw) + ei;
                         fxm |= (unsigned long long)(p ^ (p >> 63));
