@@ -426,6 +426,11 @@ def run(args):
     bytes_site = 2 * Q * esize + (8 if PRECISION in ("fp64", "fx64") else 4)
     if stencil:
         bytes_site = 24      # read Phi and the summed source, write Phi
+    # kernels per timed step: each sweep, the array-exponent update that
+    # follows every fixed-point and binary16 sweep, and one residual reduction
+    # per check (one check per step)
+    per_sweep = 2 if PRECISION in ("fx64", "fp16") and not stencil else 1
+    launches_per_step = SWEEPS_PER_STEP * per_sweep + 1
     # per-launch: plain sweeps move 2*Q*8 + 8 bytes per site
     launch_ms = dev_ms / sweeps
     achieved = V * bytes_site / (launch_ms * 1e-3) / 1e9
@@ -512,7 +517,7 @@ def run(args):
             "roofline": roofline,
             "cpu_baseline": cpu, "cpu_baseline_openmp": cpu_omp, "cpu_full_solve": cpu_full,
             "other_storage": other, "e2e": e2e, "time_to_1e8": t2e8, "serving": serving,
-            "clocks": clocks, "gpu_launches": args.steps * (SWEEPS_PER_STEP + 1),
+            "clocks": clocks, "gpu_launches": args.steps * launches_per_step,
             "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
