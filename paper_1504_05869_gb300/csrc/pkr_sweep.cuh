@@ -105,6 +105,21 @@ __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+// The copies issued since the last commit form one group.
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// Every committed group but the most recent one has landed.
+__device__ __forceinline__ void cp_async_wait_all_but_last()
+{
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+// Every committed group has landed.
+__device__ __forceinline__ void cp_async_wait_committed()
+{
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
 
 // A sweep kernel's dynamic shared memory.  The split of each SM's L1/shared
 // array is left to the driver, which takes the smallest shared part that
@@ -391,11 +406,20 @@ __device__ __forceinline__ double pow2(int e)
 // xacc, xexp: the tile's exchange rows.  after_class(std::integral_constant
 // <int, cl>) runs, in every lane, once the group's velocities of symmetry
 // class cl are relaxed and stored (classes the group holds, in order).
+// SPLIT >= 0: the group's staged values from SPLIT on may still be in flight
+// when the call starts; before_tail() (run in every lane) makes them
+// visible, and the density reads the values before SPLIT first.  The
+// fixed-point and binary64 density sums are exact, so the split leaves them
+// unchanged; binary32 runs before_tail() before its ordered sum.
 struct NoHook {
     template <class C>
     __device__ __forceinline__ void operator()(C) const {}
 };
-template <class L, typename T, int G, int g, int VS = 32 * (int)sizeof(T), class Hook = NoHook>
+struct NoTail {
+    __device__ __forceinline__ void operator()() const {}
+};
+template <class L, typename T, int G, int g, int VS = 32 * (int)sizeof(T), int SPLIT = -1,
+          class Hook = NoHook, class Tail = NoTail>
 __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
                                               const Coefs<typename AccType<T>::type>& c,
                                               int mode, bool valid, int s,
@@ -403,7 +427,8 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
                                               uint32_t sbase, int bar, long long (&xacc)[G][32],
                                               int (&xexp)[G][32], double& d2, double& n2,
                                               double& mx, double& ms, unsigned long long& fxm,
-                                              const Hook& after_class = Hook{})
+                                              const Hook& after_class = Hook{},
+                                              const Tail& before_tail = Tail{})
 {
     using R = typename AccType<T>::type;
     constexpr int lo = g * L::Q / G;
@@ -416,7 +441,15 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
     R Phi;
     if constexpr (std::is_same<T, long long>::value) {
         // fixed point: the density is an exact integer sum
-        long long part = fx_sum<n, VS, 1>(sbase);
+        long long part;
+        if constexpr (SPLIT > 0 && SPLIT < n) {
+            part = fx_sum<SPLIT, VS, 1>(sbase);
+            before_tail();
+            part += fx_sum<n - SPLIT, VS, 1>(sbase + SPLIT * VS);
+        } else {
+            if constexpr (SPLIT >= 0) before_tail();
+            part = fx_sum<n, VS, 1>(sbase);
+        }
         if constexpr (G > 1) {
             xacc[g][lane] = part;
             asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
@@ -426,7 +459,15 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
         }
         Phi = (double)part * pow2(-tg.fr);
     } else if constexpr (std::is_same<T, double>::value) {
-        int emax = max_exponent<n, VS>(sbase);
+        int emax;
+        if constexpr (SPLIT > 0 && SPLIT < n) {
+            emax = max_exponent<SPLIT, VS>(sbase);
+            before_tail();
+            emax = max(emax, max_exponent<n - SPLIT, VS>(sbase + SPLIT * VS));
+        } else {
+            if constexpr (SPLIT >= 0) before_tail();
+            emax = max_exponent<n, VS>(sbase);
+        }
         if constexpr (G > 1) {
             xexp[g][lane] = emax;
             asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(G * 32) : "memory");
@@ -454,6 +495,7 @@ __device__ __forceinline__ void group_compute(const TileGrid<T>& tg,
             Phi = plain ? __longlong_as_double(part) : fixed_value<GB>(part, emax);
         }
     } else {
+        if constexpr (SPLIT >= 0) before_tail();
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll 2
         for (int k = 0; k + 3 < n; k += 4) {

@@ -109,6 +109,14 @@ struct PairFill {
     }
 };
 
+// First velocity of the last symmetry class that velocities lo .. hi - 1 hold.
+template <class L>
+__host__ __device__ constexpr int tail_begin(int lo, int hi)
+{
+    const int b = cls_begin<L>(cls_of<L>(hi - 1));
+    return b > lo ? b : lo;
+}
+
 template <class L, typename T, int G, bool EARLY>
 __global__ void __launch_bounds__(64 * G)
 sweep_pair_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
@@ -148,12 +156,26 @@ sweep_pair_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
         fill.template pull<decltype(I)::value>(A, V, base, sub, lane, nbytes);
     };
 
+    // early refill: the copies of each symmetry class form one cp.async
+    // group, so a pair can start on every row but its group's last class
+    // (refilled last, at the end of the previous pair) while those land.
+    // Binary64 does (2.76 against 2.73 GLUPS at 256^3); fixed point and
+    // binary32 measured 0.3 % and 0.6 % slower with the split and wait for
+    // every row first.
+    constexpr bool TAIL = std::is_same<T, double>::value;
     if constexpr (EARLY) {
         if ((int)blockIdx.x < npairs) {
             fill.locate((int)blockIdx.x, nx, ny, nz, lane);
             static_for<0, G>([&](auto GI) {
                 constexpr int g = decltype(GI)::value;
-                if (grp == g) static_for<g * Q / G, (g + 1) * Q / G>(pull);
+                constexpr int lo = g * Q / G, hi = (g + 1) * Q / G;
+                constexpr int tb = tail_begin<L>(lo, hi);
+                if (grp == g) {
+                    static_for<lo, tb>(pull);
+                    if constexpr (TAIL) cp_async_commit();
+                    static_for<tb, hi>(pull);
+                    if constexpr (TAIL) cp_async_commit();
+                }
             });
         }
     }
@@ -178,22 +200,38 @@ sweep_pair_kernel(const SweepArgs a, const Coefs<typename AccType<T>::type> c)
             constexpr int g = decltype(GI)::value;
             constexpr int lo = g * Q / G, hi = (g + 1) * Q / G;
             if (grp != g) return;
-            if constexpr (!EARLY) static_for<lo, hi>(pull);
-            cp_async_wait_all();
+            if constexpr (!EARLY) {
+                static_for<lo, hi>(pull);
+                cp_async_wait_all();
+            } else if constexpr (TAIL) {
+                cp_async_wait_all_but_last();   // all rows but the last class's
+            } else {
+                cp_async_wait_all();
+            }
             // the group's other warp copied half of the values this one reads
             asm volatile("bar.sync %0, 64;" ::"r"(3 + g) : "memory");
             const uint32_t sb = base + (uint32_t)(lo * ROWB + (H + 32 * sub + lane) * ES);
             if constexpr (EARLY) {
-                group_compute<L, T, G, g, ROWB>(
+                constexpr int tb = tail_begin<L>(lo, hi);
+                group_compute<L, T, G, g, ROWB, TAIL ? tb - lo : -1>(
                     tg, c, a.mode, true, s, Sx, lane, sb, 1 + sub, xacc[par][sub], xexp[sub], rd2,
-                    rn2, rmx, rms, fxm, [&](auto CI) {
+                    rn2, rmx, rms, fxm,
+                    [&](auto CI) {
                         constexpr int cl = decltype(CI)::value;
                         constexpr int cb = cls_begin<L>(cl), ce = cls_begin<L>(cl + 1);
                         constexpr int i0 = cb > lo ? cb : lo;
                         constexpr int i1 = ce < hi ? ce : hi;
                         // both warps are done with the class's rows
                         asm volatile("bar.sync %0, 64;" ::"r"(3 + g) : "memory");
-                        if (more) static_for<i0, i1>(pull);
+                        if (more) {
+                            static_for<i0, i1>(pull);
+                            if constexpr (TAIL) cp_async_commit();
+                        }
+                    },
+                    [&]() {
+                        // the last class's rows, of both warps of the group
+                        cp_async_wait_committed();
+                        asm volatile("bar.sync %0, 64;" ::"r"(3 + g) : "memory");
                     });
             } else {
                 group_compute<L, T, G, g, ROWB>(tg, c, a.mode, true, s, Sx, lane, sb, 1 + sub,
