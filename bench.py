@@ -162,27 +162,54 @@ def kernel_label(pk, variant):
     return f"sweep_ws_kernel<{LATTICE},{T}>"
 
 
+def kernel_code_hash(texts):
+    """sha256[:16] of the sweep sources with C/C++ comments and trailing
+    blanks removed: a capture stays valid through comment edits and is void
+    once any code changes."""
+    import hashlib
+    h = hashlib.sha256()
+    for t in texts:
+        out, i, n = [], 0, len(t)
+        while i < n:
+            c = t[i]
+            if c in "\"'":                      # string or character literal
+                j = i + 1
+                while j < n and t[j] != c:
+                    j += 2 if t[j] == "\\" else 1
+                out.append(t[i:j + 1])
+                i = j + 1
+            elif t.startswith("//", i):
+                j = t.find("\n", i)
+                i = n if j < 0 else j
+            elif t.startswith("/*", i):
+                j = t.find("*/", i + 2)
+                i = n if j < 0 else j + 2
+            else:
+                out.append(c)
+                i += 1
+        code = "\n".join(line.rstrip() for line in "".join(out).splitlines())
+        h.update(code.encode())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic(variant):
     """DRAM bytes per sweep launch of the headline workload from the committed
-    ncu summary, or None if the kernel sources changed since it was taken or
+    ncu summary, or None if the kernel code changed since it was taken or
     the run launched another variant than the one captured."""
-    import hashlib
     if (SHAPE, LATTICE, ORDER) != ((256, 256, 256), "D3Q111", 5) or \
             PRECISION not in ("fp64", "fx64"):
         return None
     csrc = os.path.join(ROOT, "paper_1504_05869_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    code = kernel_code_hash(open(os.path.join(csrc, f)).read() for f in KERNEL_SOURCES)
     try:
         txt = open(os.path.join(ROOT, "profiles",
                                 f"sweep_d3q111_{PRECISION}_128cube_traffic.md")).read()
     except OSError:
         return None
     vals = dict(line.split(": ", 1) for line in txt.splitlines()
-                if line.startswith(("traffic_bytes_per_launch_256cube", "source_sha256_16",
+                if line.startswith(("traffic_bytes_per_launch_256cube", "code_sha256_16",
                                     "kernel_variant")))
-    if vals.get("source_sha256_16", "").strip() != h.hexdigest()[:16]:
+    if vals.get("code_sha256_16", "").strip() != code:
         return None
     if vals.get("kernel_variant", "").strip() != str(variant):
         return None

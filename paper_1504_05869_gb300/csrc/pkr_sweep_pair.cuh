@@ -4,8 +4,8 @@
 //
 // In the staged sweep every warp copies, for each velocity, the 32 values
 // x0 - v_x .. x0 - v_x + 31 of its row: for v_x != 0 the 256-byte run starts
-// off a 128-byte line and touches three lines, and the L1/L2 requests, not
-// DRAM, cap the sweep at about 0.72 of the copy peak for 111 velocities.
+// off a 128-byte line and touches three lines: more L1/L2 requests than a
+// whole-line run (a copy through that staging reaches 0.72 of the peak).
 // Here a block's two tiles are x-adjacent (64 sites of one row: nx a multiple
 // of 64).  For velocity i the group's two warps copy the two aligned 32-site
 // blocks x0 .. x0 + 63 of the velocity's source row, plus H halo values on
