@@ -200,7 +200,8 @@ def recorded_traffic(variant):
             PRECISION not in ("fp64", "fx64"):
         return None
     csrc = os.path.join(ROOT, "paper_1504_05869_gb300", "csrc")
-    code = kernel_code_hash(open(os.path.join(csrc, f)).read() for f in KERNEL_SOURCES)
+    code = kernel_code_hash(open(os.path.join(csrc, f), encoding="utf-8").read()
+                            for f in KERNEL_SOURCES)
     try:
         txt = open(os.path.join(ROOT, "profiles",
                                 f"sweep_d3q111_{PRECISION}_128cube_traffic.md")).read()
