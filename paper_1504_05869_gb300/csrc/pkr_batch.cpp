@@ -687,7 +687,7 @@ int round(pkr_ctx* C, std::unique_lock<std::mutex>& lk)
     if (rc == PKR_OK && cudaStreamSynchronize(C->stream) != cudaSuccess) rc = PKR_ECUDA;
     lk.lock();
     if (rc != PKR_OK) return -1;
-    // binary64 lane first, so that grids promoted in this round wait for the next window
+    // binary64 lane first, so that grids promoted in this scheduling round wait for the next window
     for (int ln = C->nlanes - 1; ln >= 0; --ln) {
         if (!ran[ln]) continue;
         Lane& L = C->lane[ln];

@@ -122,7 +122,7 @@ __device__ __forceinline__ void cp_async_wait_committed()
 }
 
 // A sweep kernel's dynamic shared memory.  The split of each SM's L1/shared
-// array is left to the driver, which takes the smallest shared part that
+// array is left to the CUDA driver, which takes the smallest shared part that
 // holds the kernel's full occupancy: the rest stays L1, where the 4- and
 // 8-byte asynchronous copies of the pull land on their way to shared memory.
 // Forcing the largest shared part (228 KB, 28 KB of L1) measured 19% slower
