@@ -68,6 +68,25 @@ def fourier_steps(S, vel, phi, chi, omega, steps):
     return np.real(np.fft.ifftn(g.sum(axis=0))).reshape(shape)
 
 
+def fourier_phi_sequence(S, vel, phi, chi, omega, steps):
+    """Phi^1 .. Phi^steps from g = 0, computed mode by mode (the recurrence
+    of fourier_steps, every step kept)."""
+    shape = np.shape(S)
+    S3 = _as3(S)
+    shape3 = S3.shape[::-1]
+    Sk = np.fft.fftn(S3)
+    E = _phases(vel, shape3)
+    ph = np.asarray(phi)[:, None, None, None]
+    ch = np.asarray(chi)[:, None, None, None]
+    g = np.zeros_like(E)
+    out = []
+    for _ in range(steps):
+        Phi = g.sum(axis=0)
+        g = E * ((1 - omega) * g + omega * ph * Phi + ch * Sk)
+        out.append(np.real(np.fft.ifftn(g.sum(axis=0))).reshape(shape))
+    return out
+
+
 def fixed_point(S, vel, phi, chi, omega):
     """Exact steady state of the scheme (closed form per Fourier mode)."""
     shape = np.shape(S)

@@ -282,3 +282,46 @@ def test_openmp_build_is_bitwise_serial():
     r1 = solve(rho, "D3Q111", 5, tau_lb=1.3, max_steps=5)
     r2 = solve(rho, "D3Q111", 5, tau_lb=1.3, max_steps=5, openmp=True)
     assert np.array_equal(r1.phi, r2.phi)
+
+
+@pytest.mark.parametrize("name,N,shape,tau,kind,every", [
+    ("D2Q81", 5, (10, 8), 1.3, 1, 5),
+    ("D2Q81", 5, (10, 8), 1.3, 0, 3),
+    ("D3Q111", 5, (6, 5, 7), 1.6, 1, 4),
+    ("D1Q13", 7, (24,), 0.9, 0, 1),
+])
+def test_stopping_step_and_residual(name, N, shape, tau, kind, every):
+    """The oracle stops at the first check (every ``every`` steps) whose
+    change of Phi over one step is below tol, and reports that change:
+    max|Phi^t - Phi^(t-1)| (kind 0) or ||Phi^t - Phi^(t-1)||_2 / ||Phi^t||_2
+    (kind 1), with Phi^t from the mode-by-mode evolution.  tol is placed
+    halfway (geometrically) between two consecutive checks, away from
+    rounding; tol <= 0 runs exactly max_steps steps and reports no check."""
+    lat = lattice(name, N)
+    rho = _rand_source(shape, 9)
+    S, _ = source(rho, lat, tau)
+    T = 240
+    seq = pins.fourier_phi_sequence(S, lat.vel, lat.phi, lat.chi, 1 / tau, T)
+
+    def change(t):                       # change over step t (t >= 2), Phi^1 from 0
+        d = seq[t - 1] - seq[t - 2]
+        if kind == 0:
+            return np.max(np.abs(d))
+        return np.linalg.norm(d) / np.linalg.norm(seq[t - 1])
+
+    checks = [t for t in range(every, T + 1, every) if t >= 2]
+    r = {t: change(t) for t in checks}
+    # the first check three decades below the first one (far above rounding)
+    # whose change is below every earlier check's
+    t_star = next(t for t in checks[1:]
+                  if r[t] < 1e-3 * r[checks[0]] and r[t] < 0.999 * min(r[u] for u in checks
+                                                                       if u < t))
+    tol = np.sqrt(r[t_star] * min(r[u] for u in checks if u < t_star))
+    want_t = next(t for t in checks if r[t] < tol)
+    res = solve(rho, name, N, tau_lb=tau, tol=tol, tol_kind=kind, check_every=every,
+                max_steps=T)
+    assert res.steps == want_t
+    assert abs(res.residual - r[want_t]) <= 1e-9 * r[want_t]
+    assert _rel(res.phi, seq[want_t - 1]) < 1e-12
+    free = solve(rho, name, N, tau_lb=tau, tol=0.0, max_steps=17)
+    assert free.steps == 17 and free.residual == -1.0
