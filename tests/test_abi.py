@@ -245,3 +245,41 @@ def test_null_handles_and_pointers_rejected(pkr):
     assert L.pkr_ctx_info(None, None, None, None, None, None) == -1
     assert L.pkr_ctx_release(None, 1) == -1
     assert L.pkr_ctx_destroy(None) == 0
+
+
+def test_struct_layouts_match_the_header(pkr, tmp_path):
+    """The ctypes mirrors of pkr_problem, pkr_stats and pkr_ctx_config have
+    the C structs' field names, order, offsets and sizes: a C program built
+    against include/pkr.h prints offsetof/sizeof of every field the binding
+    declares, and the struct sizes."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [pkr._pkr.pkr_problem, pkr._pkr.pkr_stats, pkr._pkr.pkr_ctx_config]
+    lines = ['#include <stdio.h>', '#include "pkr.h"', "int main(void) {"]
+    want = []
+    for st in structs:
+        name = st.__name__
+        lines.append(f'printf("%zu\\n", sizeof({name}));')
+        want.append(ctypes.sizeof(st))
+        for field, ftype in st._fields_:
+            lines.append(f'printf("%zu %zu\\n", offsetof({name}, {field}), '
+                         f'sizeof((({name} *)0)->{field}));')
+            want.append((getattr(st, field).offset, ctypes.sizeof(ftype)))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe],
+                   check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = []
+    for row in out:
+        parts = row.split()
+        if len(parts) == 1:
+            got.append(int(parts[0]))
+        elif len(parts) == 2:
+            got.append((int(parts[0]), int(parts[1])))
+    assert got == want
