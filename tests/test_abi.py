@@ -283,3 +283,29 @@ def test_struct_layouts_match_the_header(pkr, tmp_path):
         elif len(parts) == 2:
             got.append((int(parts[0]), int(parts[1])))
     assert got == want
+
+
+def test_enum_constants_match_the_header(pkr, tmp_path):
+    """The binding's status, lattice, precision and tolerance-kind constants
+    equal the header's enumerators (printed by a C program built against
+    include/pkr.h)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    b = pkr._pkr
+    names = [n for n in dir(b) if n.startswith("PKR_") and isinstance(getattr(b, n), int)]
+    pairs = [(n, getattr(b, n)) for n in sorted(names)]
+    pairs += [(f"PKR_{k}", v) for k, v in sorted(b.LATTICES.items())]
+    assert len(pairs) > 20
+    lines = ['#include <stdio.h>', '#include "pkr.h"', "int main(void) {"]
+    lines += [f'printf("%d\\n", (int){n});' for n, _ in pairs]
+    lines += ["return 0;", "}"]
+    src = tmp_path / "enums.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "enums")
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe],
+                   check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    assert [int(v) for v in out] == [v for _, v in pairs], pairs
